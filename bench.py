@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark: iterative-sketching least-squares solves/s on GB300.
+
+Workload (one "step" = one whole solve: sketch, Householder QR of the sketch,
+sketch-and-solve start, refinement with the Sec. 3.3 stopping rule): the
+large single FP64 problem m = 2,000,000, n = 1000 (A is 16 GB, so inputs
+exceed L2 every step), A = U diag(sigma) V^T with sigma log-spaced over
+[1e-8, 1], ||r|| = 1e-4, d = 20 n = 20000, zeta = 8, seed 0, q <= 100.
+Synthetic data, generated on the device (problems.make_problem_torch).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  With N > 1 (torchrun), every rank solves its own
+replica (independent problems: "replicas only", weak scaling) and the time is
+the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LS solves/s at ≤10× QR fwd error"
+UNIT = "solves/s"
+CFG = dict(m=2_000_000, n=1000, kappa=1e8, resnorm=1e-4, d=20_000, zeta=8, seed=0, q=100)
+WORKLOAD = ("large single FP64 problem: m=2,000,000, n=1000, kappa=1e8, ||r||=1e-4, d=20n=20000, "
+            "zeta=8, Philox seed 0, q<=100 with the Sec. 3.3 stopping rule")
+
+# FP64 FMA peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop
+# x 2.070 GHz (maximum SM clock) = 1.2586 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+# ncu DRAM traffic (read + write bytes) of one fused-pass launch on this workload,
+# keyed by the sha256 of the kernel source it was taken on; stale -> null.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ["iterate.cu", "cluster_la.cuh", "ls_internal.cuh"]:
+        with open(os.path.join(ROOT, "paper_2311_04362_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------ multi-rank
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest value over all ranks (one all-reduce; identity without a group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, ms_max: float) -> float:
+    """Whole-job solves/s: every rank solved `steps` problems; the job took the
+    slowest rank's time."""
+    return world * steps / (ms_max / 1e3)
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle timing
+def cpu_baseline(iters_hint: int | None, budget_steps: int = 1):
+    """Time the oracle (plain single-threaded C) on a bounded sample of the
+    workload and scale to seconds per full solve.  Returns (solves/s, sample
+    description, details).  The sample:
+      sketch     : oracle sketch of the first m_s = 50,000 rows (d = 20000), x m/m_s
+      QR         : oracle Householder QR + start + estimates of a 2000 x 1001
+                   sketch, x d/2000 (cost linear in d for d >> n)
+      iteration  : 2 oracle refinement steps on the m_s rows, per step x m/m_s
+      iterations : the oracle's own count on a shape-matched small problem
+                   (m = 20000, n = 100, d = 20n, same kappa and ||r||), unless
+                   the GPU run's count is given."""
+    import numpy as np
+
+    import oracle
+    import problems
+
+    oracle.build()
+    m, n, d, zeta = CFG["m"], CFG["n"], CFG["d"], CFG["zeta"]
+    ms_rows, dq = 50_000, 2000
+    P = problems.make_problem(ms_rows, n, CFG["kappa"], CFG["resnorm"], 1)
+    A, b = P["A"], P["b"]
+    t0 = time.perf_counter()
+    oracle.sketch(A, b, d, zeta, 0)
+    t_sk = time.perf_counter() - t0
+    Bq = oracle.sketch(A, b, dq, zeta, 0)
+    t0 = time.perf_counter()
+    R, x0, ne, ce, rc = oracle.factor(Bq, 0)
+    t_qr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.iterate(A, b, R, x0, 2, ne, ce, use_stop=False)
+    t_it = (time.perf_counter() - t0) / 2
+    if iters_hint is None:
+        Ps = problems.make_problem(20000, 100, CFG["kappa"], CFG["resnorm"], 2)
+        _, info = oracle.solve(Ps["A"], Ps["b"], 2000, zeta, CFG["q"], 0)
+        iters = info["iters"] + 1
+        how = "oracle count on m=20000, n=100"
+    else:
+        iters = iters_hint + 1
+        how = "GPU run's count"
+    scale_m = m / ms_rows
+    est = t_sk * scale_m + t_qr * (d / dq) + t_it * scale_m * iters
+    sample = (f"oracle on a bounded sample: sketch of {ms_rows} rows (x{scale_m:.0f}), QR of a {dq}x{n + 1} "
+              f"sketch (x{d / dq:.0f}), 2 passes over {ms_rows} rows (x{scale_m:.0f} x {iters} passes, {how}); "
+              f"estimated {est:.1f} s per solve")
+    return 1.0 / est, sample, {"t_sketch_s": t_sk, "t_qr_s": t_qr, "t_pass_s": t_it, "passes": iters,
+                               "est_s_per_solve": est}
+
+
+# --------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--check-qr", action="store_true", help="also compute the Householder-QR forward error (slow)")
+    ap.add_argument("--case", choices=["solve", "pass"], default="solve",
+                    help="pass: only the fused residual/gradient pass on an m x 1000 problem (for ncu captures)")
+    ap.add_argument("--m", type=int, default=200_000, help="rows for --case pass")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+    if args.case == "pass":
+        return pass_case(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    import problems
+
+    torch.cuda.set_device(local_rank)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+
+    from paper_2311_04362_gb300 import build
+    build.build()
+    m, n, d, zeta, seed, q = CFG["m"], CFG["n"], CFG["d"], CFG["zeta"], CFG["seed"], CFG["q"]
+    P = problems.make_problem_torch(m, n, CFG["kappa"], CFG["resnorm"], CFG["seed"] + rank, device="cuda")
+    A, b, xtrue = P["A"], P["b"], P["x"]
+    stream = torch.cuda.current_stream()
+    ctx = ls.Context(local_rank, stream)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    for _ in range(args.warmup):
+        ctx.ls_solve(A, b, m, n, n, d, zeta, q, seed, x)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        st, info = ctx.ls_solve(A, b, m, n, n, d, zeta, q, seed, x)
+        infos.append((st, ls.ls_info.from_buffer_copy(info)))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda")
+    value = job_throughput(world, args.steps, ms_max)
+
+    fe = float(torch.linalg.norm(x - xtrue) / torch.linalg.norm(xtrue))
+    statuses = sorted({ls.STATUS_NAMES[s] for s, _ in infos})
+    iters = [i.iters for _, i in infos]
+    pass_ms = sum(i.ms_pass for _, i in infos) / max(1, sum(i.n_pass for _, i in infos))
+    launches = sum(i.launches for _, i in infos)
+    flops = 4.0 * m * n
+    alg_bytes = 8.0 * m * (n + 3)
+    achieved_tflops = flops / (pass_ms / 1e3) / 1e12
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    khash = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get(khash)
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        Ah.copy_(A)
+        bh = torch.empty(m, dtype=torch.float64, pin_memory=True)
+        bh.copy_(b)
+        xh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        ctx.ls_solve(Ah, bh, m, n, n, d, zeta, q, seed, xh)    # warm the staging buffer
+        k2 = args.e2e_steps or max(1, args.steps // 2)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k2):
+            ctx.ls_solve(Ah, bh, m, n, n, d, zeta, q, seed, xh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms2 = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+        e2e = {"value": job_throughput(world, k2, ms2), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * m * n + 8 * m, "d2h_bytes_per_step": 8 * n, "steps": k2,
+               "fe": float(np.linalg.norm(xh.numpy() - xtrue.cpu().numpy()) / np.linalg.norm(xtrue.cpu().numpy()))}
+        del Ah, bh
+
+    fe_qr = None
+    if args.check_qr and rank == 0:
+        import oracle
+        t0 = time.perf_counter()
+        xq = oracle.qr_solve_lapack(A.cpu().numpy(), b.cpu().numpy())
+        fe_qr = {"fe_qr": oracle.forward_error(xq, xtrue.cpu().numpy()), "seconds": time.perf_counter() - t0}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, det = cpu_baseline(int(statistics.median(iters)))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, **det}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": m, "n": n, "d": d, "zeta": zeta, "kappa": CFG["kappa"],
+                       "resnorm": CFG["resnorm"], "q": q, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (A is 16 GB per step)"},
+            "roofline": {"bound": "alu", "kernel": "k_fused_pass", "achieved": achieved_tflops,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz",
+                         "traffic": traffic, "algorithmic_flops": flops, "algorithmic_bytes": alg_bytes,
+                         "pass_ms": pass_ms,
+                         "hbm_view": {"achieved_gbs": alg_bytes / (pass_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                                      "frac": alg_bytes / (pass_ms / 1e3) / 1e9 / hbm_peak,
+                                      "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+                         "kernel_source_hash": khash},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "accuracy": {"fe": fe, "status": statuses, "iters": iters, **(fe_qr or {})},
+            "phase_ms": {"sketch": statistics.mean(i.ms_sketch for _, i in infos),
+                         "factor": statistics.mean(i.ms_factor for _, i in infos),
+                         "iterate": statistics.mean(i.ms_iterate for _, i in infos)},
+            "latency_ms": {"p50": statistics.median([i.ms_sketch + i.ms_factor + i.ms_iterate for _, i in infos]),
+                           "max": max(i.ms_sketch + i.ms_factor + i.ms_iterate for _, i in infos)},
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def pass_case(args):
+    """Fused residual/gradient pass alone (ls_residual_gradient) on an
+    m x 1000 row-major A (default m = 200,000: 1.6 GB, larger than L2):
+    warm-up passes, then timed passes with CUDA events on the launching
+    stream.  Used for small-case ncu captures of k_fused_pass."""
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    from paper_2311_04362_gb300 import build
+
+    build.build()
+    m, n = args.m, 1000
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    A = torch.randn(m, n, dtype=torch.float64, device="cuda", generator=g)
+    b = torch.randn(m, dtype=torch.float64, device="cuda", generator=g)
+    x = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    r = torch.zeros(m, dtype=torch.float64, device="cuda")
+    c = torch.empty(n, dtype=torch.float64, device="cuda")
+    norms = torch.empty(2, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    with ls.Context(0, stream) as ctx:
+        for _ in range(args.warmup):
+            ctx.ls_residual_gradient(A, m, n, n, b, x, r, r, c, norms)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.ls_residual_gradient(A, m, n, n, b, x, r, r, c, norms)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"case": "fused pass", "m": m, "n": n, "ms_per_call": ms,
+                      "tflops": 4.0 * m * n / (ms / 1e3) / 1e12,
+                      "gbs": 8.0 * m * (n + 3) / (ms / 1e3) / 1e9}))
+
+
+def reference_arm(args, world, rank):
+    """The oracle (CPU, as it stands) timed on this arm's workload: each step
+    is the bounded-sample estimate of one solve (see cpu_baseline)."""
+    if rank != 0:
+        return
+    vals, samples, det = [], None, None
+    for i in range(args.warmup + args.steps):
+        v, samples, det = cpu_baseline(None)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, **{k: CFG[k] for k in ("m", "n", "d", "zeta", "kappa", "resnorm", "q")}},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": samples, **det},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * ls.h -- C ABI of libls, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of iterative sketching for overdetermined linear
+ * least squares (E. N. Epperly, "Fast and forward stable randomized algorithms
+ * for linear least-squares problems", arXiv:2311.04362).
+ *
+ * Problem (Sec. 1, Eq. (1.1)): x = argmin_y ||b - A y||, A m x n, m >= n,
+ * full rank.  Method (Algorithm 2, "Iterative sketching"):
+ *     S   d x m sparse sign embedding                 (Sec. 2.2, Eq. (2.4))
+ *     B = S A, Sb = S b                                (sketch)
+ *     (Q, R) = QR(B, 'econ')                          (Sec. 3.2, Eq. (3.4))
+ *     x0 = R^{-1} (Q^T (S b))                         (Sec. 2.3, Eq. (2.5))
+ *     repeat: r = b - A x; c = A^T r; d = R^{-1}(R^{-T} c); x = x + d
+ * with the stopping rule of Sec. 3.3.
+ *
+ * Conventions for every call below
+ *  - Every array argument is a pointer the caller owns.  Unless a call says
+ *    otherwise it must be DEVICE memory of the context's device.  No call keeps
+ *    a pointer after it returns.
+ *  - A is row-major: A[j*lda + k] is entry (j, k); lda >= n, lda even, and A
+ *    16-byte aligned (rows are streamed with 16-byte bulk copies).
+ *  - B (the sketch) and R are column-major: B[t + c*ldb], R[i + j*ldr].
+ *  - All calls run on the context's CUDA stream and RETURN AFTER THE WORK HAS
+ *    FINISHED (each call synchronises that stream), so output arrays and the
+ *    host-side ls_info are valid on return.
+ *  - Calls never throw; they return an ls_status.  On any status other than
+ *    LS_OK the outputs are unspecified and ls_last_error() gives a message.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef LS_H
+#define LS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LS_API __attribute__((visibility("default")))
+#else
+#define LS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LS_OK = 0,
+    LS_EINVAL = 1,      /* invalid argument (sizes, leading dims, alignment, null) */
+    LS_ENOMEM = 2,      /* device or pinned-host allocation failed */
+    LS_ECUDA = 3,       /* a CUDA runtime call failed */
+    LS_ERANK = 4,       /* R[k,k] of the sketch is zero or not finite (rank deficient) */
+    LS_ENONFINITE = 5,  /* a non-finite value appeared in the iterate */
+    LS_ETIMEOUT = 6,    /* a bounded device-side wait gave up (pipeline stalled) */
+    LS_ENOTCONV = 7     /* q updates done and the stopping rule never held; x is still the q-th iterate */
+} ls_status;
+
+typedef struct ls_ctx ls_ctx;   /* opaque: device, stream, device scratch arena */
+
+typedef struct {
+    int   iters;        /* updates x <- x + d applied by this call */
+    int   stop_reason;  /* 0: stopping rule held, 1: q reached, 2: stop rule off */
+    double res_norm;    /* ||r(x_i)|| of the last residual formed */
+    double step_norm;   /* ||r(x_i) - r(x_{i-1})|| of the last step tested */
+    double normest;     /* estimate of ||R||_2 (Sec. 3.3) */
+    double condest;     /* estimate of kappa_1(R) (Sec. 3.3) */
+    float ms_sketch, ms_factor, ms_iterate;   /* device time of each phase (ls_solve) */
+    float ms_pass;      /* device time of the fused passes that did work (CUDA events) */
+    int   n_pass;       /* number of those passes */
+    int   launches;     /* kernels this call launched */
+} ls_info;
+
+typedef struct {
+    double gamma;       /* Sec. 3.3 stopping rule, default 1.0 */
+    double rho;         /* Sec. 3.3 stopping rule, default 0.04 */
+    int extra_iters;    /* updates to run after the rule first holds, default 0 */
+    int use_stop;       /* 1: apply the stopping rule (default), 0: run exactly q updates */
+    double alpha;       /* App. B, Eq. (B.1) step weight; 1.0 = Algorithm 2 */
+    double beta;        /* App. B, Eq. (B.1) momentum weight; 0.0 = Algorithm 2 */
+} ls_opts;
+
+/* Default options: gamma 1, rho 0.04, extra 0, stop on, alpha 1, beta 0. */
+LS_API void ls_default_opts(ls_opts* opts);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * the calls run on (0: a new non-blocking stream owned by the context).
+ * LS_ECUDA if the device is not an sm_103 GPU or the kernels fail to load. */
+LS_API ls_status ls_create(ls_ctx** ctx, int device, void* cuda_stream);
+
+/* Free the context and its device scratch.  NULL is accepted. */
+LS_API ls_status ls_destroy(ls_ctx* ctx);
+
+/* Text of the last error on this context ("" after a successful call). */
+LS_API const char* ls_last_error(const ls_ctx* ctx);
+
+/* Device scratch bytes the context needs for a solve of this shape (for
+ * admission against an HBM budget).  Excludes the caller's A, b, x. */
+LS_API size_t ls_workspace_bytes(int64_t m, int64_t n, int64_t d, int zeta);
+
+/* (a1) Sparse sign embedding indices, Sec. 2.2, Eq. (2.4): for each column
+ * j < m of S, zeta distinct rows in [0, d), ascending, written to
+ * rows[j*zeta .. j*zeta+zeta-1]; signs[j] bit k is the sign of the k-th
+ * smallest row (1 means -1).  Generated from Philox4x32-10 keyed by `seed`
+ * (counter (j lo, j hi, block, 0)); bit-identical for a given (m, d, zeta,
+ * seed).  rows: m*zeta int32, signs: m uint32 (device).
+ * LS_EINVAL unless 1 <= zeta <= min(d, 32), d <= 2^31-1, m <= 2^31-1. */
+LS_API ls_status ls_sketch_indices(ls_ctx* ctx, int64_t m, int64_t d, int zeta, uint64_t seed,
+                            int32_t* rows, uint32_t* signs);
+
+/* (a2) Counting sort of the m*zeta nonzeros of S by sketch row, stable in the
+ * column index: row_ptr (d+1 int64) and ent (m*zeta uint32) with
+ * ent[e] = (j << 1) | (sign < 0) for the e-th nonzero, ascending j inside
+ * each sketch row.  Inputs are ls_sketch_indices outputs (device). */
+LS_API ls_status ls_sketch_csr(ls_ctx* ctx, int64_t m, int64_t d, int zeta,
+                        const int32_t* rows, const uint32_t* signs,
+                        int64_t* row_ptr, uint32_t* ent);
+
+/* (a1-a3) B_aug = S [A b] (Algorithm 2, sketch step): B column-major
+ * d x (n+1), ldb >= d; column n holds S b.  Entry (t, c) is
+ * (1/sqrt(zeta)) * (sum over column indices j of sketch row t, ascending, of
+ * +-A[j, c]) with the sum taken left to right from +0.0; no floating-point
+ * atomics, so the result is bit-identical run to run. */
+LS_API ls_status ls_sketch(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda,
+                    const double* b, int64_t d, int zeta, uint64_t seed,
+                    double* B, int64_t ldb);
+
+/* (a4-a5) Householder QR of B_aug in place (Sec. 3.2, Eq. (3.4)); writes the
+ * upper-triangular R (n x n, column-major, ldr >= n; strictly-lower part set
+ * to zero), the sketch-and-solve start x0 = R^{-1} (Q^T S b)[0:n]
+ * (Sec. 2.3, Eq. (2.5)), and in info (may be NULL) normest (ceil(ln n) power
+ * steps on R, start vector from Philox keyed by `seed`) and condest
+ * (||R||_1 times Hager's estimate of ||R^{-1}||_1), the estimates of Sec. 3.3.
+ * The diagonal of R may be negative.  LS_ERANK if some R[k,k] is zero or
+ * not finite.  B is overwritten with the Householder vectors. */
+LS_API ls_status ls_factor(ls_ctx* ctx, double* B, int64_t d, int64_t n, int64_t ldb,
+                    double* R, int64_t ldr, double* x0, uint64_t seed, ls_info* info);
+
+/* (a6) One fused residual/gradient pass over A (Algorithm 2 loop body):
+ * r = b - A x and c = A^T r, reading A from HBM once.  c: n doubles;
+ * norms[0] = ||r||^2, norms[1] = ||r - r_prev||^2 (0 if r_prev is NULL).
+ * r_out (m doubles) may be NULL; r_prev (m doubles) may be NULL and may equal
+ * r_out (then it is read before being overwritten).  Sums are taken in a
+ * fixed order, so the results are bit-identical run to run. */
+LS_API ls_status ls_residual_gradient(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda,
+                               const double* b, const double* x, const double* r_prev,
+                               double* r_out, double* c, double* norms);
+
+/* (a7) The correction of Algorithm 2: y = R^{-T} c, d = R^{-1} y (two
+ * triangular solves), x <- x + d.  y_out, d_out (n doubles) may be NULL. */
+LS_API ls_status ls_correct(ls_ctx* ctx, const double* R, int64_t ldr, int64_t n, const double* c,
+                     double* x, double* y_out, double* d_out);
+
+/* (a6-a7) Iterate from x (in: start, out: final iterate), at most q updates,
+ * with the Sec. 3.3 stopping rule (opts may be NULL for defaults).
+ * normest/condest come from ls_factor (pass info from ls_factor, or set
+ * info->normest/condest); info must not be NULL.  Resumable: calling twice
+ * with q1 then q2 and use_stop = 0 equals one call with q1 + q2.
+ * Returns LS_OK when the rule held, LS_ENOTCONV when q updates ran without
+ * it (x valid), LS_ENONFINITE if x became non-finite. */
+LS_API ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda,
+                     const double* b, const double* R, int64_t ldr, double* x, int q,
+                     const ls_opts* opts, ls_info* info);
+
+/* The whole method: sketch, factor, start, iterate (q <= 0 means 100).
+ * A, b and x may be HOST or DEVICE pointers (detected per pointer); host
+ * arrays are copied to context-owned device memory and x is copied back.
+ * info may be NULL.  Status as ls_iterate. */
+LS_API ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n,
+                   int64_t lda, int64_t d, int zeta, int q, uint64_t seed, double* x,
+                   ls_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LS_H */

@@ -278,3 +278,16 @@ def solve(A, b, d: int, zeta: int, q: int, seed: int, *, use_stop: bool = True, 
 
 def forward_error(x_hat, x) -> float:
     return float(np.linalg.norm(x - x_hat) / np.linalg.norm(x))
+
+
+def qr_solve_lapack(A, b):
+    """Householder QR least-squares solve through LAPACK (numpy.linalg.qr is
+    dgeqrf/dorgqr, blocked Householder) -- the same method as ``qr_solve``
+    for matrices too large for the plain loops.  x = R^{-1} (Q^T b)."""
+    import scipy.linalg as sl
+
+    A = np.asarray(A, dtype=np.float64)
+    Q, R = np.linalg.qr(A, mode="reduced")
+    z = Q.T @ np.asarray(b, dtype=np.float64)
+    del Q
+    return sl.solve_triangular(R, z, lower=False)

@@ -1,0 +1,649 @@
+// api.cu -- the extern "C" entry points declared in include/ls.h: argument
+// checks, the context's scratch arena, and the order of kernel launches for
+// each step of Algorithm 2 (sketch, factor, start, iterate).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "ls_internal.cuh"
+
+using namespace lsk;
+
+namespace {
+
+ls_status fail(ls_ctx* ctx, ls_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                                       \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      if (e_ == cudaErrorMemoryAllocation) return fail(ctx, LS_ENOMEM, "%s: %s", #call, cudaGetErrorString(e_)); \
+      return fail(ctx, LS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));                     \
+    }                                                                                             \
+  } while (0)
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bump allocator over the context arena; `plan` first measures, then carves.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += align256(count * sizeof(T));
+    return p;
+  }
+};
+
+ls_status ensure_arena(ls_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->arena_bytes) return LS_OK;
+  if (ctx->arena) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->arena);
+    ctx->arena = nullptr;
+    ctx->arena_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  if (cudaMalloc(&ctx->arena, want) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, LS_ENOMEM, "device scratch of %zu bytes could not be allocated", want);
+  }
+  ctx->arena_bytes = want;
+  return LS_OK;
+}
+
+ls_status ensure_stage(ls_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->stage_bytes) return LS_OK;
+  if (ctx->stage) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+  }
+  if (cudaMalloc(&ctx->stage, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, LS_ENOMEM, "device staging of %zu bytes could not be allocated", bytes);
+  }
+  ctx->stage_bytes = bytes;
+  return LS_OK;
+}
+
+// Separate buffer for the large-bucket sort scratch (sized after the
+// histogram, so growing it never moves the arena).
+ls_status ensure_aux(ls_ctx* ctx, void** aux, size_t* aux_bytes, size_t bytes) {
+  if (bytes <= *aux_bytes) return LS_OK;
+  if (*aux) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(*aux);
+    *aux = nullptr;
+    *aux_bytes = 0;
+  }
+  if (cudaMalloc(aux, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, LS_ENOMEM, "sort scratch of %zu bytes could not be allocated", bytes);
+  }
+  *aux_bytes = bytes;
+  return LS_OK;
+}
+
+// status word handling -------------------------------------------------------
+ls_status reset_status(ls_ctx* ctx) {
+  CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, 4 * sizeof(unsigned int), ctx->stream));
+  return LS_OK;
+}
+
+ls_status sync_and_check(ls_ctx* ctx) {
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  const unsigned int st = *reinterpret_cast<unsigned int*>(ctx->h_pinned);
+  if (st & LS_DEV_TIMEOUT) return fail(ctx, LS_ETIMEOUT, "a bounded device wait gave up (pipeline stalled)");
+  if (st & LS_DEV_RANK) return fail(ctx, LS_ERANK, "R has a zero or non-finite diagonal entry (rank deficient)");
+  if (st & LS_DEV_NONFINITE) return fail(ctx, LS_ENONFINITE, "the iterate became non-finite");
+  if (st & LS_DEV_BADSIZE) return fail(ctx, LS_ECUDA, "internal: sort scratch missing for a large bucket");
+  return LS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// argument checks -------------------------------------------------------------
+ls_status check_sketch_args(ls_ctx* ctx, int64_t m, int64_t d, int zeta) {
+  if (m < 1 || m > INT32_MAX) return fail(ctx, LS_EINVAL, "m = %lld out of range [1, 2^31-1]", (long long)m);
+  if (d < 1 || d > INT32_MAX) return fail(ctx, LS_EINVAL, "d = %lld out of range [1, 2^31-1]", (long long)d);
+  if (zeta < 1 || zeta > 32 || zeta > d)
+    return fail(ctx, LS_EINVAL, "zeta = %d must satisfy 1 <= zeta <= min(d, 32)", zeta);
+  return LS_OK;
+}
+
+ls_status check_A(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda) {
+  if (!A) return fail(ctx, LS_EINVAL, "A is null");
+  if (n < 1 || n > m) return fail(ctx, LS_EINVAL, "need 1 <= n <= m (n = %lld, m = %lld)", (long long)n, (long long)m);
+  if (lda < n || (lda & 1)) return fail(ctx, LS_EINVAL, "lda = %lld must be even and >= n", (long long)lda);
+  if (reinterpret_cast<uintptr_t>(A) & 15) return fail(ctx, LS_EINVAL, "A must be 16-byte aligned");
+  return LS_OK;
+}
+
+constexpr int64_t kMaxN = 2048;   // fused pass keeps up to 8 columns per thread
+
+// scratch layouts ---------------------------------------------------------------
+struct SketchScratch {
+  int32_t* rows; uint32_t* signs; int64_t* row_ptr; uint32_t* ent; unsigned long long* fill;
+};
+SketchScratch carve_sketch(Carve& c, int64_t m, int64_t d, int zeta) {
+  SketchScratch s;
+  s.rows = c.take<int32_t>((size_t)m * zeta);
+  s.signs = c.take<uint32_t>((size_t)m);
+  s.row_ptr = c.take<int64_t>((size_t)d + 1);
+  s.ent = c.take<uint32_t>((size_t)m * zeta);
+  s.fill = c.take<unsigned long long>((size_t)d);
+  return s;
+}
+
+struct FactorScratch {
+  double* part; double* w; double* Rt; double* inv_diag; double* vecs; double* est;
+};
+FactorScratch carve_factor(Carve& c, const ls_ctx* ctx, int64_t d, int64_t n) {
+  FactorScratch f;
+  f.part = c.take<double>(householder_part_doubles(ctx, d, n));
+  f.w = c.take<double>((size_t)n + 2);
+  f.Rt = c.take<double>((size_t)n * n);
+  f.inv_diag = c.take<double>((size_t)n);
+  f.vecs = c.take<double>(4 * (size_t)n + 64);
+  f.est = c.take<double>(2);
+  return f;
+}
+
+struct IterScratch {
+  double* part; double* Rt; double* inv_diag; double* x_prev; double* y; double* dvec; double* work;
+  double* slots; IterState* st; double* r_prev;
+};
+IterScratch carve_iter(Carve& c, const PassGeom& g, int64_t m, int64_t n) {
+  IterScratch s;
+  s.part = c.take<double>((size_t)g.grid * (n + 2));
+  s.Rt = c.take<double>((size_t)n * n);
+  s.inv_diag = c.take<double>((size_t)n);
+  s.x_prev = c.take<double>((size_t)n);
+  s.y = c.take<double>((size_t)n);
+  s.dvec = c.take<double>((size_t)n);
+  s.work = c.take<double>((size_t)n);
+  s.slots = c.take<double>(64);
+  s.st = c.take<IterState>(1);
+  s.r_prev = c.take<double>((size_t)m);
+  return s;
+}
+
+}  // namespace
+
+// ============================================================ public API
+extern "C" {
+
+void ls_default_opts(ls_opts* o) {
+  if (!o) return;
+  o->gamma = 1.0;
+  o->rho = 0.04;
+  o->extra_iters = 0;
+  o->use_stop = 1;
+  o->alpha = 1.0;
+  o->beta = 0.0;
+}
+
+ls_status ls_create(ls_ctx** out, int device, void* cuda_stream) {
+  if (!out) return LS_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return LS_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return LS_EINVAL;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return LS_ECUDA;
+  if (prop.major != 10 || prop.minor != 3) return LS_ECUDA;   // built for sm_103a only
+  ls_ctx* ctx = new ls_ctx();
+  ctx->device = device;
+  ctx->num_sms = prop.multiProcessorCount;
+  if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return LS_ECUDA; }
+  if (cuda_stream) {
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return LS_ECUDA; }
+    ctx->own_stream = true;
+  }
+  if (cudaMalloc(&ctx->d_status, 16 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_misc, 16 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_pinned, 4096) != cudaSuccess) {
+    ls_destroy(ctx);
+    return LS_ENOMEM;
+  }
+  cudaMemset(ctx->d_status, 0, 16 * sizeof(unsigned int));
+  for (auto& e : ctx->ev) cudaEventCreate(&e);
+  ctx->cluster = 8;
+  *out = ctx;
+  return LS_OK;
+}
+
+ls_status ls_destroy(ls_ctx* ctx) {
+  if (!ctx) return LS_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_misc) cudaFree(ctx->d_misc);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  for (auto& e : ctx->ev) if (e) cudaEventDestroy(e);
+  for (auto& e : ctx->pass_ev) if (e) cudaEventDestroy(e);
+  if (ctx->aux) cudaFree(ctx->aux);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return LS_OK;
+}
+
+const char* ls_last_error(const ls_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t ls_workspace_bytes(int64_t m, int64_t n, int64_t d, int zeta) {
+  if (m < 1 || n < 1 || d < 1 || zeta < 1) return 0;
+  ls_ctx probe;
+  probe.num_sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) probe.num_sms = p.multiProcessorCount;
+  }
+  cudaGetLastError();
+  Carve c(nullptr);
+  c.take<double>((size_t)d * (n + 1));   // B_aug
+  c.take<double>((size_t)n * n);         // R
+  c.take<double>((size_t)n);             // x0
+  const size_t mark = c.off;
+  carve_sketch(c, m, d, zeta);
+  size_t sk = c.off;
+  c.off = mark;
+  carve_factor(c, &probe, d, n);
+  size_t fa = c.off;
+  c.off = mark;
+  PassGeom g = pass_geometry(&probe, n, m);
+  carve_iter(c, g, m, n);
+  size_t it = c.off;
+  size_t need = std::max(sk, std::max(fa, it));
+  return need;
+}
+
+ls_status ls_sketch_indices(ls_ctx* ctx, int64_t m, int64_t d, int zeta, uint64_t seed, int32_t* rows,
+                            uint32_t* signs) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st = check_sketch_args(ctx, m, d, zeta);
+  if (st) return st;
+  if (!rows || !signs) return fail(ctx, LS_EINVAL, "rows/signs are null");
+  cudaSetDevice(ctx->device);
+  if ((st = reset_status(ctx))) return st;
+  CUDA_TRY(ctx, launch_sketch_indices(ctx, m, d, zeta, seed, rows, signs));
+  return sync_and_check(ctx);
+}
+
+static ls_status sketch_csr_impl(ls_ctx* ctx, int64_t m, int64_t d, int zeta, const int32_t* rows,
+                                 const uint32_t* signs, int64_t* row_ptr, uint32_t* ent, unsigned long long* fill) {
+  int maxb = 0;
+  CUDA_TRY(ctx, launch_sketch_csr(ctx, m, d, zeta, rows, signs, row_ptr, ent, fill, nullptr, &maxb));
+  uint32_t* scratch = nullptr;
+  int P = 1;
+  while (P < maxb) P <<= 1;
+  if (P > sketch_sort_cap()) {
+    ls_status st = ensure_aux(ctx, &ctx->aux, &ctx->aux_bytes, sizeof(uint32_t) * 2 * (size_t)m * zeta);
+    if (st) return st;
+    scratch = reinterpret_cast<uint32_t*>(ctx->aux);
+  }
+  // histogram + scan again (cheap) and then scatter + sort
+  CUDA_TRY(ctx, launch_sketch_csr(ctx, m, d, zeta, rows, signs, row_ptr, ent, fill, scratch, nullptr));
+  return LS_OK;
+}
+
+ls_status ls_sketch_csr(ls_ctx* ctx, int64_t m, int64_t d, int zeta, const int32_t* rows, const uint32_t* signs,
+                        int64_t* row_ptr, uint32_t* ent) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st = check_sketch_args(ctx, m, d, zeta);
+  if (st) return st;
+  if (!rows || !signs || !row_ptr || !ent) return fail(ctx, LS_EINVAL, "null pointer argument");
+  cudaSetDevice(ctx->device);
+  Carve c(nullptr);
+  unsigned long long* fill_probe = c.take<unsigned long long>((size_t)d);
+  (void)fill_probe;
+  if ((st = ensure_arena(ctx, c.off))) return st;
+  Carve cc(ctx->arena);
+  unsigned long long* fill = cc.take<unsigned long long>((size_t)d);
+  if ((st = reset_status(ctx))) return st;
+  if ((st = sketch_csr_impl(ctx, m, d, zeta, rows, signs, row_ptr, ent, fill))) return st;
+  return sync_and_check(ctx);
+}
+
+static ls_status sketch_impl(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                             int64_t d, int zeta, uint64_t seed, double* B, int64_t ldb, Carve& cc) {
+  SketchScratch s = carve_sketch(cc, m, d, zeta);
+  CUDA_TRY(ctx, launch_sketch_indices(ctx, m, d, zeta, seed, s.rows, s.signs));
+  ls_status st = sketch_csr_impl(ctx, m, d, zeta, s.rows, s.signs, s.row_ptr, s.ent, s.fill);
+  if (st) return st;
+  const double scale = 1.0 / std::sqrt((double)zeta);
+  CUDA_TRY(ctx, launch_sketch_apply(ctx, A, m, n, lda, b, d, s.row_ptr, s.ent, scale, B, ldb));
+  return LS_OK;
+}
+
+ls_status ls_sketch(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
+                    int zeta, uint64_t seed, double* B, int64_t ldb) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st;
+  if ((st = check_sketch_args(ctx, m, d, zeta))) return st;
+  if ((st = check_A(ctx, A, m, n, lda))) return st;
+  if (!b || !B) return fail(ctx, LS_EINVAL, "b/B is null");
+  if (ldb < d) return fail(ctx, LS_EINVAL, "ldb < d");
+  if (d < n) return fail(ctx, LS_EINVAL, "d = %lld must be >= n = %lld", (long long)d, (long long)n);
+  cudaSetDevice(ctx->device);
+  Carve probe(nullptr);
+  carve_sketch(probe, m, d, zeta);
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  if ((st = reset_status(ctx))) return st;
+  if ((st = sketch_impl(ctx, A, m, n, lda, b, d, zeta, seed, B, ldb, cc))) return st;
+  return sync_and_check(ctx);
+}
+
+static ls_status factor_impl(ls_ctx* ctx, double* B, int64_t d, int64_t n, int64_t ldb, double* R, int64_t ldr,
+                             double* x0, uint64_t seed, Carve& cc, double* est_host) {
+  FactorScratch f = carve_factor(cc, ctx, d, n);
+  CUDA_TRY(ctx, launch_householder(ctx, B, d, n, ldb, f.part, f.w));
+  CUDA_TRY(ctx, launch_prepare_R(ctx, B, ldb, n, R, ldr, f.Rt, f.inv_diag));
+  CUDA_TRY(ctx, launch_post_factor(ctx, B, d, n, ldb, R, ldr, x0, seed, f.Rt, f.inv_diag, f.vecs, f.est));
+  CUDA_TRY(ctx, cudaMemcpyAsync(reinterpret_cast<char*>(ctx->h_pinned) + 64, f.est, 2 * sizeof(double),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+  ls_status st = sync_and_check(ctx);
+  if (st) return st;
+  std::memcpy(est_host, reinterpret_cast<char*>(ctx->h_pinned) + 64, 2 * sizeof(double));
+  return LS_OK;
+}
+
+ls_status ls_factor(ls_ctx* ctx, double* B, int64_t d, int64_t n, int64_t ldb, double* R, int64_t ldr, double* x0,
+                    uint64_t seed, ls_info* info) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  if (!B || !R || !x0) return fail(ctx, LS_EINVAL, "null pointer argument");
+  if (n < 1 || d < n) return fail(ctx, LS_EINVAL, "need 1 <= n <= d");
+  if (ldb < d || ldr < n) return fail(ctx, LS_EINVAL, "ldb < d or ldr < n");
+  if (n > 1000000) return fail(ctx, LS_EINVAL, "n too large");
+  cudaSetDevice(ctx->device);
+  ls_status st;
+  Carve probe(nullptr);
+  carve_factor(probe, ctx, d, n);
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  if ((st = reset_status(ctx))) return st;
+  double est[2];
+  const long long l0 = ctx->launches;
+  st = factor_impl(ctx, B, d, n, ldb, R, ldr, x0, seed, cc, est);
+  if (st) return st;
+  if (info) {
+    std::memset(info, 0, sizeof *info);
+    info->normest = est[0];
+    info->condest = est[1];
+    info->launches = (int)(ctx->launches - l0);
+  }
+  return LS_OK;
+}
+
+ls_status ls_residual_gradient(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                               const double* x, const double* r_prev, double* r_out, double* c, double* norms) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st;
+  if (m < 1) return fail(ctx, LS_EINVAL, "m must be >= 1");
+  if ((st = check_A(ctx, A, m, n, lda))) return st;
+  if (n > kMaxN) return fail(ctx, LS_EINVAL, "n = %lld above the fused-pass limit %lld", (long long)n, (long long)kMaxN);
+  if (!b || !x || !c || !norms) return fail(ctx, LS_EINVAL, "null pointer argument");
+  cudaSetDevice(ctx->device);
+  PassGeom g = pass_geometry(ctx, n, m);
+  Carve probe(nullptr);
+  probe.take<double>((size_t)g.grid * (n + 2));
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  double* part = cc.take<double>((size_t)g.grid * (n + 2));
+  CUtensorMap map;
+  CUDA_TRY(ctx, make_tensor_map(ctx, &map, A, m, n, lda, g));
+  if ((st = reset_status(ctx))) return st;
+  CUDA_TRY(ctx, launch_fused_pass(ctx, map, g, m, n, b, x, r_prev, r_out, part, nullptr));
+  CUDA_TRY(ctx, launch_reduce_partials(ctx, part, g.grid, n, c, norms));
+  if (!r_prev) CUDA_TRY(ctx, cudaMemsetAsync(norms + 1, 0, sizeof(double), ctx->stream));
+  return sync_and_check(ctx);
+}
+
+ls_status ls_correct(ls_ctx* ctx, const double* R, int64_t ldr, int64_t n, const double* c, double* x, double* y_out,
+                     double* d_out) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  if (!R || !c || !x) return fail(ctx, LS_EINVAL, "null pointer argument");
+  if (n < 1 || ldr < n) return fail(ctx, LS_EINVAL, "need n >= 1 and ldr >= n");
+  cudaSetDevice(ctx->device);
+  ls_status st;
+  Carve probe(nullptr);
+  probe.take<double>((size_t)n * n);
+  for (int i = 0; i < 4; ++i) probe.take<double>((size_t)n);
+  probe.take<double>(64);
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  StepArgs a{};
+  double* Rt = cc.take<double>((size_t)n * n);
+  double* inv_diag = cc.take<double>((size_t)n);
+  a.y = cc.take<double>((size_t)n);
+  a.dvec = cc.take<double>((size_t)n);
+  a.work = cc.take<double>((size_t)n);
+  a.slots = cc.take<double>(64);
+  a.Rt = Rt; a.R = R; a.ldr = ldr; a.inv_diag = inv_diag; a.n = (int)n;
+  a.x = x; a.c_in = c; a.y_out = y_out; a.d_out = d_out; a.status = ctx->d_status;
+  if ((st = reset_status(ctx))) return st;
+  CUDA_TRY(ctx, launch_prepare_R(ctx, R, ldr, n, nullptr, n, Rt, inv_diag));
+  CUDA_TRY(ctx, launch_correct(ctx, a));
+  return sync_and_check(ctx);
+}
+
+static ls_status iterate_impl(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                              const double* R, int64_t ldr, double* x, int q, const ls_opts* opts, double normest,
+                              double condest, Carve& cc, ls_info* info) {
+  ls_opts o;
+  ls_default_opts(&o);
+  if (opts) o = *opts;
+  PassGeom g = pass_geometry(ctx, n, m);
+  IterScratch s = carve_iter(cc, g, m, n);
+  CUtensorMap map;
+  CUDA_TRY(ctx, make_tensor_map(ctx, &map, A, m, n, lda, g));
+  CUDA_TRY(ctx, launch_prepare_R(ctx, R, ldr, n, nullptr, n, s.Rt, s.inv_diag));
+  IterState h{};
+  h.gamma = o.gamma; h.rho = o.rho; h.alpha = o.alpha; h.beta = o.beta;
+  h.normest = normest; h.condest = condest;
+  IterState* hs = reinterpret_cast<IterState*>(reinterpret_cast<char*>(ctx->h_pinned) + 256);
+  *hs = h;
+  CUDA_TRY(ctx, cudaMemcpyAsync(s.st, hs, sizeof(IterState), cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(s.x_prev, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(s.r_prev, 0, sizeof(double) * m, ctx->stream));
+  StepArgs a{};
+  a.part = s.part; a.nparts = g.grid; a.Rt = s.Rt; a.R = R; a.ldr = ldr; a.inv_diag = s.inv_diag; a.n = (int)n;
+  a.x = x; a.x_prev = s.x_prev; a.y = s.y; a.dvec = s.dvec; a.work = s.work; a.slots = s.slots; a.st = s.st;
+  a.use_stop = o.use_stop; a.extra = o.extra_iters; a.status = ctx->d_status;
+  // launch in chunks; between chunks read the done flag.  Each fused pass is
+  // bracketed by two events on the launching stream (its device time).
+  if ((int)ctx->pass_ev.size() < 2 * q) {
+    const size_t old = ctx->pass_ev.size();
+    ctx->pass_ev.resize(2 * (size_t)q);
+    for (size_t i = old; i < ctx->pass_ev.size(); ++i) CUDA_TRY(ctx, cudaEventCreate(&ctx->pass_ev[i]));
+  }
+  const int chunk = 8;
+  int launched = 0;
+  IterState* hread = reinterpret_cast<IterState*>(reinterpret_cast<char*>(ctx->h_pinned) + 1024);
+  while (launched < q) {
+    const int k = std::min(chunk, q - launched);
+    for (int i = 0; i < k; ++i) {
+      CUDA_TRY(ctx, cudaEventRecord(ctx->pass_ev[2 * (launched + i)], ctx->stream));
+      CUDA_TRY(ctx, launch_fused_pass(ctx, map, g, m, n, b, x, s.r_prev, s.r_prev, s.part, s.st));
+      CUDA_TRY(ctx, cudaEventRecord(ctx->pass_ev[2 * (launched + i) + 1], ctx->stream));
+      CUDA_TRY(ctx, launch_iter_step(ctx, a));
+    }
+    launched += k;
+    if (launched < q) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(hread, s.st, sizeof(IterState), cudaMemcpyDeviceToHost, ctx->stream));
+      CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      if (hread->done) break;
+    }
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(hread, s.st, sizeof(IterState), cudaMemcpyDeviceToHost, ctx->stream));
+  ls_status st = sync_and_check(ctx);
+  if (st) return st;
+  const bool by_rule = hread->done && !hread->nonfinite;
+  const int active = std::min(launched, by_rule ? hread->iter + 1 : hread->iter);
+  float ms_pass = 0.0f;
+  for (int i = 0; i < active; ++i) {
+    float ms = 0.0f;
+    CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->pass_ev[2 * i], ctx->pass_ev[2 * i + 1]));
+    ms_pass += ms;
+  }
+  if (info) {
+    info->iters = hread->iter;
+    info->res_norm = hread->rnorm;
+    info->step_norm = hread->dnorm;
+    info->normest = normest;
+    info->condest = condest;
+    info->stop_reason = hread->done ? (hread->nonfinite ? 3 : 0) : (o.use_stop ? 1 : 2);
+    info->ms_pass = ms_pass;
+    info->n_pass = active;
+  }
+  if (hread->nonfinite) return fail(ctx, LS_ENONFINITE, "the iterate became non-finite");
+  if (!hread->done && o.use_stop) return LS_ENOTCONV;
+  return LS_OK;
+}
+
+ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                     const double* R, int64_t ldr, double* x, int q, const ls_opts* opts, ls_info* info) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st;
+  if (m < 1) return fail(ctx, LS_EINVAL, "m must be >= 1");
+  if ((st = check_A(ctx, A, m, n, lda))) return st;
+  if (n > kMaxN) return fail(ctx, LS_EINVAL, "n = %lld above the fused-pass limit %lld", (long long)n, (long long)kMaxN);
+  if (!b || !R || !x || !info) return fail(ctx, LS_EINVAL, "null pointer argument (info is required)");
+  if (ldr < n) return fail(ctx, LS_EINVAL, "ldr < n");
+  if (q < 0) return fail(ctx, LS_EINVAL, "q < 0");
+  cudaSetDevice(ctx->device);
+  PassGeom g = pass_geometry(ctx, n, m);
+  Carve probe(nullptr);
+  carve_iter(probe, g, m, n);
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  if ((st = reset_status(ctx))) return st;
+  const double ne = info->normest, ce = info->condest;
+  const long long l0 = ctx->launches;
+  st = iterate_impl(ctx, A, m, n, lda, b, R, ldr, x, q, opts, ne, ce, cc, info);
+  info->launches = (int)(ctx->launches - l0);
+  return st;
+}
+
+ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n, int64_t lda, int64_t d,
+                   int zeta, int q, uint64_t seed, double* x, ls_info* info) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st;
+  if ((st = check_sketch_args(ctx, m, d, zeta))) return st;
+  if (!A || !b || !x) return fail(ctx, LS_EINVAL, "null pointer argument");
+  if (n < 1 || n > m) return fail(ctx, LS_EINVAL, "need 1 <= n <= m");
+  if (lda < n || (lda & 1)) return fail(ctx, LS_EINVAL, "lda must be even and >= n");
+  if (d < n) return fail(ctx, LS_EINVAL, "d must be >= n");
+  if (n > kMaxN) return fail(ctx, LS_EINVAL, "n = %lld above the fused-pass limit %lld", (long long)n, (long long)kMaxN);
+  if (q <= 0) q = 100;
+  cudaSetDevice(ctx->device);
+  const bool dA = is_device_ptr(A), db = is_device_ptr(b), dx = is_device_ptr(x);
+  // staging for host arrays
+  size_t stage = 0;
+  if (!dA) stage += align256(sizeof(double) * (size_t)m * lda);
+  if (!db) stage += align256(sizeof(double) * (size_t)m);
+  if (!dx) stage += align256(sizeof(double) * (size_t)n);
+  if (stage && (st = ensure_stage(ctx, stage))) return st;
+  if (dA && (reinterpret_cast<uintptr_t>(A) & 15)) return fail(ctx, LS_EINVAL, "A must be 16-byte aligned");
+  Carve sc(ctx->stage);
+  const double* Ad = A;
+  const double* bd = b;
+  double* xd = x;
+  if (!dA) {
+    double* p = sc.take<double>((size_t)m * lda);
+    CUDA_TRY(ctx, cudaMemcpyAsync(p, A, sizeof(double) * (size_t)m * lda, cudaMemcpyHostToDevice, ctx->stream));
+    Ad = p;
+  }
+  if (!db) {
+    double* p = sc.take<double>((size_t)m);
+    CUDA_TRY(ctx, cudaMemcpyAsync(p, b, sizeof(double) * (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
+    bd = p;
+  }
+  if (!dx) xd = sc.take<double>((size_t)n);
+
+  // arena: B_aug, R | max(sketch, factor, iterate) scratch
+  Carve probe(nullptr);
+  probe.take<double>((size_t)d * (n + 1));
+  probe.take<double>((size_t)n * n);
+  const size_t mark = probe.off;
+  carve_sketch(probe, m, d, zeta);
+  size_t need = probe.off;
+  probe.off = mark;
+  carve_factor(probe, ctx, d, n);
+  need = std::max(need, probe.off);
+  probe.off = mark;
+  PassGeom g = pass_geometry(ctx, n, m);
+  carve_iter(probe, g, m, n);
+  need = std::max(need, probe.off);
+  if ((st = ensure_arena(ctx, need))) return st;
+  Carve cc(ctx->arena);
+  double* B = cc.take<double>((size_t)d * (n + 1));
+  double* R = cc.take<double>((size_t)n * n);
+  const size_t mark2 = cc.off;
+  if ((st = reset_status(ctx))) return st;
+
+  const long long l0 = ctx->launches;
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+  if ((st = sketch_impl(ctx, Ad, m, n, lda, bd, d, zeta, seed, B, d, cc))) return st;
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+  cc.off = mark2;
+  double est[2];
+  if ((st = factor_impl(ctx, B, d, n, d, R, n, xd, seed, cc, est))) return st;
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
+  cc.off = mark2;
+  ls_info local{};
+  ls_status it = iterate_impl(ctx, Ad, m, n, lda, bd, R, n, xd, q, nullptr, est[0], est[1], cc, &local);
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], ctx->stream));
+  if (it != LS_OK && it != LS_ENOTCONV) return it;
+  if (!dx) CUDA_TRY(ctx, cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (info) {
+    *info = local;
+    cudaEventElapsedTime(&info->ms_sketch, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&info->ms_factor, ctx->ev[1], ctx->ev[2]);
+    cudaEventElapsedTime(&info->ms_iterate, ctx->ev[2], ctx->ev[3]);
+    info->launches = (int)(ctx->launches - l0);
+  }
+  return it;
+}
+
+}  // extern "C"

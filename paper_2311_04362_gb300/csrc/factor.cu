@@ -1,0 +1,361 @@
+// factor.cu -- Householder QR of the sketch B_aug = [S A  S b] (Algorithm 2,
+// QR step; Sec. 3.2, Eq. (3.4)), the sketch-and-solve start
+// x0 = R^{-1} (Q^T S b) (Sec. 2.3, Eq. (2.5)) and the two estimates of the
+// Sec. 3.3 stopping rule.
+//
+// k_householder: one cooperative launch, P CTAs, each owning a contiguous
+// slice of the d rows.  Column k is reduced with three bounded grid barriers:
+//   1. partial sums of squares of column k below the diagonal  -> barrier
+//   2. every CTA forms the same reflector (fixed-order sum of the partials),
+//      scales its slice of v, and forms partial dots v^T B[:, j]  -> barrier
+//   3. CTA p reduces the dots of columns j with (j-k-1) mod P == p -> barrier
+//   4. every CTA updates its slice: B[:, j] -= (tau w_j) v
+// The reflector convention is LAPACK's (beta = -sign(alpha) ||x||, sign(0) = +,
+// tau = (beta - alpha)/beta, v = x / (alpha - beta) with v_k = 1); the same
+// reflectors are applied to column n (S b), which yields Q^T S b.
+//
+// k_prepare_R: R (upper, strictly-lower part zeroed), its transpose Rt and
+// the reciprocal diagonal used by every later substitution.
+//
+// k_post_factor: one thread-block cluster.  Solves R x0 = (Q^T S b)[0:n],
+// runs ceil(ln n) power steps on R (normest) and Hager's 1-norm estimator of
+// ||R^{-1}||_1 times ||R||_1 (condest).
+#include "cluster_la.cuh"
+
+namespace lsk {
+
+__global__ void __launch_bounds__(256) k_householder(double* __restrict__ B, int64_t d, int n, int64_t ldb,
+                                                     double* __restrict__ part, double* __restrict__ w,
+                                                     GridBar gb) {
+  extern __shared__ double vs[];  // this CTA's slice of the current v
+  __shared__ double s_ab[4];      // alpha, beta, tau, scal
+  __shared__ int s_bad;
+  const int P = gridDim.x, p = blockIdx.x;
+  const int ncols = n + 1;
+  const int64_t chunk = (d + P - 1) / P;
+  const int64_t r0 = (int64_t)p * chunk, r1 = min(d, r0 + chunk);
+  const int PS = ncols + 1;          // stride of one CTA's partials
+  double* alpha_slot = part + (size_t)P * PS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+
+  for (int k = 0; k < n; ++k) {
+    // ---- phase 1: partial ||B[k+1:, k]||^2, publish alpha
+    const int64_t lo = max(r0, (int64_t)k + 1);
+    double ss = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < r1; i += blockDim.x) {
+      const double v = B[i + (int64_t)k * ldb];
+      ss += v * v;
+    }
+    ss = cta_sum(ss);
+    if (threadIdx.x == 0) {
+      __stcg(part + (size_t)p * PS, ss);
+      if (k >= r0 && k < r1) __stcg(alpha_slot, B[k + (int64_t)k * ldb]);
+    }
+    if (!grid_sync(gb, P)) return;
+
+    // ---- phase 2: reflector (identical in every CTA), scale v, partial dots
+    if (warp == 0) {
+      double t = 0.0;
+      for (int q = lane; q < P; q += 32) t += __ldcg(part + (size_t)q * PS);
+      t = warp_sum(t);
+      if (lane == 0) {
+        const double alpha = __ldcg(alpha_slot);
+        const double xnorm = sqrt(t);
+        double beta, tau, scal;
+        if (xnorm == 0.0) {
+          beta = alpha; tau = 0.0; scal = 1.0;
+        } else {
+          const double h = hypot(alpha, xnorm);
+          beta = (alpha >= 0.0) ? -h : h;
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
+        s_ab[0] = alpha; s_ab[1] = beta; s_ab[2] = tau; s_ab[3] = scal;
+        s_bad = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    if (s_bad) {
+      if (p == 0 && threadIdx.x == 0) atomicOr(gb.status, LS_DEV_RANK);
+      return;   // every CTA takes the same decision
+    }
+    const double tau = s_ab[2], scal = s_ab[3];
+    const int64_t vlo = max(r0, (int64_t)k);   // rows of v in this slice (v_k = 1)
+    for (int64_t i = vlo + threadIdx.x; i < r1; i += blockDim.x) {
+      double v;
+      if (i == k) {
+        v = 1.0;
+      } else {
+        v = B[i + (int64_t)k * ldb];
+        if (tau != 0.0) { v = v * scal; B[i + (int64_t)k * ldb] = v; }
+      }
+      vs[i - r0] = v;
+    }
+    if (threadIdx.x == 0 && k >= r0 && k < r1) B[k + (int64_t)k * ldb] = s_ab[1];
+    __syncthreads();
+    for (int j = k + 1 + warp; j < ncols; j += nwarp) {
+      double s = 0.0;
+      if (tau != 0.0)
+        for (int64_t i = vlo + lane; i < r1; i += 32) s += vs[i - r0] * B[i + (int64_t)j * ldb];
+      s = warp_sum(s);
+      if (lane == 0) __stcg(part + (size_t)p * PS + 1 + j, s);
+    }
+    if (!grid_sync(gb, P)) return;
+
+    // ---- phase 3: w_j = sum over CTAs (fixed order), columns dealt round robin
+    if (tau != 0.0) {
+      for (int j = k + 1 + p * nwarp + warp; j < ncols; j += P * nwarp) {
+        double s = 0.0;
+        for (int q = lane; q < P; q += 32) s += __ldcg(part + (size_t)q * PS + 1 + j);
+        s = warp_sum(s);
+        if (lane == 0) __stcg(w + j, s);
+      }
+    }
+    if (!grid_sync(gb, P)) return;
+
+    // ---- phase 4: B[:, j] -= (tau w_j) v on this slice
+    if (tau != 0.0) {
+      for (int j = k + 1 + warp; j < ncols; j += nwarp) {
+        const double tw = tau * __ldcg(w + j);
+        for (int64_t i = vlo + lane; i < r1; i += 32) {
+          double* bp = B + i + (int64_t)j * ldb;
+          *bp = *bp - tw * vs[i - r0];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ prepare R
+// src: upper triangle of a column-major matrix (lds).  Writes R_out (if not
+// null, ldr), Rt[a + b*n] = R[b, a], inv_diag[i] = 1 / R[i, i].
+__global__ void k_prepare_R(const double* __restrict__ src, int64_t lds, int n, double* __restrict__ R_out,
+                            int64_t ldr, double* __restrict__ Rt, double* __restrict__ inv_diag,
+                            unsigned int* __restrict__ status) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / n), i = (int)(e - (int64_t)j * n);
+    const double r = (i <= j) ? src[i + (int64_t)j * lds] : 0.0;
+    if (R_out) R_out[i + (int64_t)j * ldr] = r;
+    Rt[(size_t)j + (size_t)i * n] = r;
+    if (i == j) {
+      inv_diag[i] = 1.0 / r;
+      if (r == 0.0 || !isfinite(r)) atomicOr(status, LS_DEV_RANK);
+    }
+  }
+}
+
+cudaError_t launch_prepare_R(ls_ctx* ctx, const double* src, int64_t lds, int64_t n, double* R_out, int64_t ldr,
+                             double* Rt, double* inv_diag) {
+  const int64_t total = n * n;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 8);
+  k_prepare_R<<<grid, 256, 0, ctx->stream>>>(src, lds, (int)n, R_out, ldr, Rt, inv_diag, ctx->d_status);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ post factor
+struct PostArgs {
+  const double* B; int64_t ldb; int n;
+  const double* R; int64_t ldr;
+  const double* Rt; const double* inv_diag;
+  double* x0; uint64_t seed;
+  double* v; double* w; double* xi; double* work;   // n-vectors
+  double* slots;                                     // 2 * ncta
+  double* est;                                       // [normest, condest]
+  unsigned int* status;
+};
+
+__device__ inline double sgn1(double v) { return v >= 0.0 ? 1.0 : -1.0; }
+
+__device__ inline double power_start(uint64_t seed, uint32_t domain, int i) {
+  WordStream s(seed, (uint64_t)i, domain);
+  const uint32_t w0 = s.next(), w1 = s.next();
+  const uint64_t bits = ((uint64_t)w0 << 21) | (uint64_t)(w1 >> 11);
+  return 2.0 * ((double)bits * 0x1.0p-53) - 1.0;
+}
+
+// w = R v (rows i of R, from Rt) for owned rows.
+__device__ inline void cl_matvec_R(const CL& cl, const double* Rt, int n, const double* v, double* w) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nb = (n + 31) / 32;
+  for (int b = cl.rank; b < nb; b += cl.ncta)
+    for (int i = 32 * b + warp; i < min(n, 32 * b + 32); i += nw) {
+      double s = 0.0;
+      for (int k = i + lane; k < n; k += 32) s += __ldg(Rt + (size_t)k + (size_t)i * n) * __ldcg(v + k);
+      s = warp_sum(s);
+      if (lane == 0) __stcg(w + i, s);
+    }
+}
+
+// v = R^T w (column i of R) for owned rows.
+__device__ inline void cl_matvec_RT(const CL& cl, const double* R, int64_t ldr, int n, const double* w, double* v) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nb = (n + 31) / 32;
+  for (int b = cl.rank; b < nb; b += cl.ncta)
+    for (int i = 32 * b + warp; i < min(n, 32 * b + 32); i += nw) {
+      double s = 0.0;
+      for (int k = lane; k <= i; k += 32) s += __ldg(R + (size_t)k + (size_t)i * ldr) * __ldcg(w + k);
+      s = warp_sum(s);
+      if (lane == 0) __stcg(v + i, s);
+    }
+}
+
+__device__ inline int power_steps(int n) {
+  int k = 0;
+  while (k < 64 && exp((double)k) < (double)n) ++k;
+  return k < 1 ? 1 : k;
+}
+
+__global__ void __launch_bounds__(256) k_post_factor(PostArgs a) {
+  const CL cl = cl_this();
+  const int n = a.n;
+  const int nb = (n + 31) / 32;
+  // ---- x0 = R^{-1} z, z = (Q^T S b)[0:n] = column n of the factored B
+  cl_load_owned(cl, n, a.B + (int64_t)n * a.ldb, a.work);
+  cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, a.x0);
+
+  // ---- normest: power method on R^T R from a Philox start vector
+  for_owned_rows(cl, n, [&](int i) { __stcg(a.v + i, power_start(a.seed, 1u, i)); });
+  cl_sync();
+  double nv = cl_norm2(cl, n, a.v, a.slots);
+  for_owned_rows(cl, n, [&](int i) { __stcg(a.v + i, __ldcg(a.v + i) / nv); });
+  cl_sync();
+  const int steps = power_steps(n);
+  for (int st = 0; st < steps; ++st) {
+    cl_matvec_R(cl, a.Rt, n, a.v, a.w);
+    cl_sync();
+    cl_matvec_RT(cl, a.R, a.ldr, n, a.w, a.v);
+    cl_sync();
+    nv = cl_norm2(cl, n, a.v, a.slots);
+    for_owned_rows(cl, n, [&](int i) { __stcg(a.v + i, __ldcg(a.v + i) / nv); });
+    cl_sync();
+  }
+  cl_matvec_R(cl, a.Rt, n, a.v, a.w);
+  cl_sync();
+  const double normest = cl_norm2(cl, n, a.w, a.slots);
+
+  // ---- condest = ||R||_1 * Hager estimate of ||R^{-1}||_1
+  double colmax = 0.0;
+  (void)nb;
+  for (int b = cl.rank; b < nb; b += cl.ncta)
+    for (int j = 32 * b + (int)threadIdx.x; j < min(n, 32 * b + 32); j += blockDim.x) {
+      double s = 0.0;
+      for (int i = 0; i <= j; ++i) s += fabs(__ldg(a.R + i + (int64_t)j * a.ldr));
+      colmax = fmax(colmax, s);
+    }
+  const double norm1 = cl_max(cl, cta_max(colmax), a.slots);
+
+  double* x = a.v;   // reuse
+  double* y = a.w;
+  for_owned_rows(cl, n, [&](int i) { __stcg(a.work + i, 1.0 / (double)n); });
+  __syncthreads();
+  cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, y);      // y = R^{-1} x
+  double est;
+  if (n == 1) {
+    est = fabs(__ldcg(y));
+  } else {
+    est = cl_norm1(cl, n, y, a.slots);
+    for_owned_rows(cl, n, [&](int i) { __stcg(a.xi + i, sgn1(__ldcg(y + i))); });
+    cl_sync();
+    cl_load_owned(cl, n, a.xi, a.work);
+    cl_solve_RT(cl, a.Rt, n, a.inv_diag, a.work, x);         // x = R^{-T} xi
+    int j = cl_argmax_abs(cl, n, x, a.slots);
+    int iter = 2;
+    for (;;) {
+      for_owned_rows(cl, n, [&](int i) { __stcg(a.work + i, i == j ? 1.0 : 0.0); });
+      __syncthreads();
+      cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, y);  // y = R^{-1} e_j
+      const double est_old = est;
+      est = cl_norm1(cl, n, y, a.slots);
+      double diff = 0.0;
+      for_owned_rows(cl, n, [&](int i) { if (sgn1(__ldcg(y + i)) != __ldcg(a.xi + i)) diff = 1.0; });
+      const double any_diff = cl_max(cl, cta_max(diff), a.slots);
+      if (any_diff == 0.0 || est <= est_old) break;
+      for_owned_rows(cl, n, [&](int i) { __stcg(a.xi + i, sgn1(__ldcg(y + i))); });
+      cl_sync();
+      cl_load_owned(cl, n, a.xi, a.work);
+      cl_solve_RT(cl, a.Rt, n, a.inv_diag, a.work, x);       // x = R^{-T} xi
+      const int jlast = j;
+      j = cl_argmax_abs(cl, n, x, a.slots);
+      if (__ldcg(x + jlast) != fabs(__ldcg(x + j)) && iter < 5) { iter += 1; continue; }
+      break;
+    }
+    for_owned_rows(cl, n, [&](int i) {
+      const double v = 1.0 + (double)i / (double)(n - 1);
+      __stcg(a.work + i, (i % 2 == 0) ? v : -v);
+    });
+    __syncthreads();
+    cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, y);
+    double alt = cl_norm1(cl, n, y, a.slots);
+    alt = 2.0 * alt / (3.0 * (double)n);
+    if (alt > est) est = alt;
+  }
+  if (cl.rank == 0 && threadIdx.x == 0) {
+    a.est[0] = normest;
+    a.est[1] = norm1 * est;
+  }
+}
+
+// ------------------------------------------------------------ host side
+int householder_ctas(const ls_ctx* ctx, int64_t d) {
+  int64_t p = (d + 63) / 64;
+  if (p > ctx->num_sms) p = ctx->num_sms;
+  if (p < 1) p = 1;
+  return (int)p;
+}
+
+cudaError_t launch_householder(ls_ctx* ctx, double* B, int64_t d, int64_t n, int64_t ldb, double* part,
+                               double* w) {
+  const int P = householder_ctas(ctx, d);
+  const int64_t chunk = (d + P - 1) / P;
+  const size_t smem = (size_t)chunk * sizeof(double);
+  cudaError_t e;
+  if (smem > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+  }
+  if ((e = cudaMemsetAsync(ctx->d_status + 1, 0, 2 * sizeof(unsigned int), ctx->stream)) != cudaSuccess) return e;
+  GridBar gb{ctx->d_status + 1, ctx->d_status + 2, ctx->d_status};
+  int nn = (int)n;
+  void* args[] = {&B, &d, &nn, &ldb, &part, &w, &gb};
+  ++ctx->launches;
+  return cudaLaunchCooperativeKernel((const void*)k_householder, dim3(P), dim3(256), args, smem, ctx->stream);
+}
+
+size_t householder_part_doubles(const ls_ctx* ctx, int64_t d, int64_t n) {
+  return (size_t)householder_ctas(ctx, d) * (size_t)(n + 2) + 1;
+}
+
+cudaError_t launch_cluster(ls_ctx* ctx, const void* fn, void** args, int cluster) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++ctx->launches;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+cudaError_t launch_post_factor(ls_ctx* ctx, const double* B, int64_t d, int64_t n, int64_t ldb, const double* R,
+                               int64_t ldr, double* x0, uint64_t seed, const double* Rt, const double* inv_diag,
+                               double* vecs /* 4n + 64 */, double* est_out) {
+  (void)d;
+  PostArgs a;
+  a.B = B; a.ldb = ldb; a.n = (int)n; a.R = R; a.ldr = ldr; a.Rt = Rt; a.inv_diag = inv_diag;
+  a.x0 = x0; a.seed = seed;
+  a.v = vecs; a.w = vecs + n; a.xi = vecs + 2 * n; a.work = vecs + 3 * n; a.slots = vecs + 4 * n;
+  a.est = est_out; a.status = ctx->d_status;
+  void* args[] = {&a};
+  return launch_cluster(ctx, (const void*)k_post_factor, args, ctx->cluster);
+}
+
+}  // namespace lsk

@@ -1,0 +1,389 @@
+// iterate.cu -- the refinement loop of Algorithm 2:
+//     r = b - A x,  c = A^T r,  d = R^{-1} (R^{-T} c),  x <- x + d
+// with the Sec. 3.3 stopping rule and the App. B (Eq. (B.1)) damping /
+// momentum update.
+//
+// k_fused_pass (a6): persistent, one CTA per SM.  A is streamed in row tiles
+// (tr rows x all columns) by TMA (cp.async.bulk.tensor.2d) into a ring of
+// shared-memory stages fed by one producer warp; eight consumer warps use each
+// tile twice -- first each warp forms the row dots A_j x (lanes over columns,
+// warp-shuffle tree) and r_j = b_j - A_j x, then every thread adds r_j A_jk to
+// its own columns of c -- so A is read from HBM exactly once per pass.  Each
+// CTA writes one partial (c, ||r||^2, ||r - r_prev||^2); partials are summed
+// over CTAs in index order by the next kernel, so results are bit-identical
+// run to run.  Every wait is bounded by %globaltimer.
+//
+// k_iter_step / k_correct (a7): one thread-block cluster sums the partials,
+// applies the stopping rule and performs the two triangular solves
+// (cluster_la.cuh) and the update.
+#include "cluster_la.cuh"
+
+namespace lsk {
+
+static constexpr int kConsumerWarps = 8;
+static constexpr int kThreads = (kConsumerWarps + 1) * 32;
+
+struct PassArgs {
+  int64_t m;
+  int n, boxw, nbox, tr, stages, ntiles;
+  const double* b;
+  const double* x;
+  const double* r_prev;    // may be null
+  double* r_out;           // may be null (may equal r_prev)
+  double* part;            // gridDim.x * (n + 2)
+  const IterState* st;     // null: always run
+  unsigned int* status;
+};
+
+// Shared-memory offset (in doubles) of element (row r, column c) of a tile.
+__device__ inline int tile_off(int r, int c, int boxw, int nbox, int tr) {
+  return (nbox == 1) ? (r * boxw + c) : ((c >> 8) * (tr * 256) + r * 256 + (c & 255));
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constant__ CUtensorMap map, PassArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (a.st && a.st->done) return;
+  const int n = a.n, tr = a.tr, boxw = a.boxw, nbox = a.nbox, S = a.stages;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t stage_doubles = (size_t)tr * nbox * boxw;
+  // layout: [stages][stage_doubles] tiles | x[n] | rtile[2][tr] | red[...] | bars
+  double* tiles = reinterpret_cast<double*>(smem_raw);
+  double* xs = tiles + S * stage_doubles;
+  double* rtile = xs + ((n + 1) & ~1);
+  double* red = rtile + 2 * tr;                     // 2 * kConsumerWarps + 8
+  uint64_t* full = reinterpret_cast<uint64_t*>(red + 2 * kConsumerWarps + 8);
+  uint64_t* empty = full + S;
+  __shared__ int s_abort;
+
+  const int G = (n >= 256) ? 1 : max(1, 256 / n);   // row groups in phase 2 (n < 256)
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], kConsumerWarps); }
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  for (int i = tid; i < n; i += blockDim.x) xs[i] = a.x[i];
+  __syncthreads();
+
+  const uint32_t tile_bytes = (uint32_t)(stage_doubles * sizeof(double));
+  const uint64_t deadline = gtimer() + LS_WAIT_NS;
+
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      prefetch_tmap(&map);
+      int k = 0;
+      for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+        const int s = k % S;
+        if (k >= S) {
+          if (!mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1, deadline)) {
+            atomicOr(a.status, LS_DEV_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+        }
+        mbar_arrive_expect_tx(&full[s], tile_bytes);
+        double* dst = tiles + (size_t)s * stage_doubles;
+        for (int q = 0; q < nbox; ++q) tma_load_2d(dst + (size_t)q * tr * boxw, &map, q * boxw, t * tr, &full[s]);
+      }
+      // drain: wait until every issued copy has landed before the CTA can exit
+      const int issued = k;
+      for (int kk = max(0, issued - S); kk < issued; ++kk)
+        mbar_wait_bounded(&full[kk % S], (kk / S) & 1, deadline + LS_WAIT_NS);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  double acc[NPT];
+#pragma unroll
+  for (int u = 0; u < NPT; ++u) acc[u] = 0.0;
+  double rn2 = 0.0, dn2 = 0.0;               // lane-0 accumulators per warp
+  const int g = tid / max(n, 1);             // phase-2 row group (n < 256)
+  const int cg = tid - g * n;                // phase-2 column (n < 256)
+
+  int k = 0;
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+    const int s = k % S;
+    if (!mbar_wait_bounded(&full[s], (k / S) & 1, deadline)) {
+      atomicOr(a.status, LS_DEV_TIMEOUT);
+      break;
+    }
+    const double* tl = tiles + (size_t)s * stage_doubles;
+    double* rt = rtile + (k & 1) * tr;
+    const int64_t row0 = (int64_t)t * tr;
+    const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
+
+    // phase 1: r_j = b_j - A_j x, one warp per row
+    for (int r = warp; r < tr; r += kConsumerWarps) {
+      double dot = 0.0, bj = 0.0, rpj = 0.0;
+      if (lane == 0 && r < rows) {           // issue the row's loads before the dot
+        bj = a.b[row0 + r];
+        if (a.r_prev) rpj = a.r_prev[row0 + r];
+      }
+      if (r < rows) {
+        for (int c = lane; c < n; c += 32) dot += tl[tile_off(r, c, boxw, nbox, tr)] * xs[c];
+      }
+      dot = warp_sum(dot);
+      if (lane == 0) {
+        double rj = 0.0;
+        if (r < rows) {
+          const int64_t j = row0 + r;
+          rj = bj - dot;
+          rn2 += rj * rj;
+          if (a.r_prev) { const double dl = rj - rpj; dn2 += dl * dl; }
+          if (a.r_out) a.r_out[j] = rj;
+        }
+        rt[r] = rj;
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32));
+
+    // phase 2: c_k += A_jk r_j over the tile's rows
+    if (NPT > 1 || n >= 256) {
+      for (int r = 0; r < rows; ++r) {
+        const double rj = rt[r];
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) {
+          const int c = tid + 256 * u;
+          if (c < n) acc[u] += tl[tile_off(r, c, boxw, nbox, tr)] * rj;
+        }
+      }
+    } else if (g < G) {
+      for (int r = g; r < rows; r += G) acc[0] += tl[r * boxw + cg] * rt[r];
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+
+  // ------------------------------------------------- per-CTA partial out
+  double* out = a.part + (size_t)blockIdx.x * (n + 2);
+  if (n >= 256 || NPT > 1) {
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+      const int c = tid + 256 * u;
+      if (c < n) out[c] = acc[u];
+    }
+  } else {
+    // reduce the G row groups of each column in group order (tile memory is
+    // free now: all stages consumed)
+    double* gsum = tiles;
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32));
+    if (g < G) gsum[g * n + cg] = acc[0];
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32));
+    for (int c = tid; c < n; c += kConsumerWarps * 32) {
+      double sum = 0.0;
+      for (int q = 0; q < G; ++q) sum += gsum[q * n + c];
+      out[c] = sum;
+    }
+  }
+  if (lane == 0) { red[warp] = rn2; red[kConsumerWarps + warp] = dn2; }
+  asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32));
+  if (tid == 0) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < kConsumerWarps; ++w) { s1 += red[w]; s2 += red[kConsumerWarps + w]; }
+    out[n] = s1;
+    out[n + 1] = s2;
+  }
+  (void)s_abort;
+}
+
+// Sum the per-CTA partials in CTA order: c[k], norms[0..1].
+__global__ void k_reduce_partials(const double* __restrict__ part, int nparts, int n, double* __restrict__ c,
+                                  double* __restrict__ norms) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n + 2) return;
+  double s = 0.0;
+  for (int p = 0; p < nparts; ++p) s += part[(size_t)p * (n + 2) + k];
+  if (k < n) c[k] = s;
+  else norms[k - n] = s;
+}
+
+// ------------------------------------------------------------ cluster steps
+// Sum partial column k over CTAs (fixed order).
+__device__ inline double part_sum(const double* part, int nparts, int n, int k) {
+  double s = 0.0;
+  for (int p = 0; p < nparts; ++p) s += __ldcg(part + (size_t)p * (n + 2) + k);
+  return s;
+}
+
+__global__ void __launch_bounds__(256) k_iter_step(StepArgs a) {
+  const CL cl = cl_this();
+  const int n = a.n;
+  IterState S = *a.st;       // every CTA reads the state before anyone writes it
+  cl_sync();
+  if (S.done) return;
+
+  // ||r_i||, ||r_i - r_{i-1}|| (every CTA computes them identically)
+  __shared__ double s_norm[2];
+  if (threadIdx.x < 2) s_norm[threadIdx.x] = part_sum(a.part, a.nparts, n, n + threadIdx.x);
+  __syncthreads();
+  const double rnorm = sqrt(s_norm[0]);
+  const double dnorm = S.have_prev ? sqrt(s_norm[1]) : 0.0;
+  const double u = 0x1.0p-53;
+  int fired = S.fired, extra_left = S.extra_left, done = 0;
+  if (a.use_stop && S.have_prev && !fired) {
+    if (dnorm <= u * (S.gamma * S.normest * S.xnorm + S.rho * S.condest * rnorm)) {
+      fired = 1;
+      extra_left = a.extra;
+    }
+  }
+  if (fired) {
+    if (extra_left == 0) done = 1;
+    else extra_left -= 1;
+  }
+  if (done) {
+    if (cl.rank == 0 && threadIdx.x == 0) {
+      a.st->done = 1; a.st->fired = 1; a.st->stop_reason = 0;
+      a.st->rnorm = rnorm; a.st->dnorm = dnorm;
+    }
+    return;
+  }
+
+  // c = sum of partials for the owned rows -> forward solve y = R^{-T} c
+  for_owned_rows(cl, n, [&](int i) { __stcg(a.work + i, part_sum(a.part, a.nparts, n, i)); });
+  __syncthreads();
+  cl_solve_RT(cl, a.Rt, n, a.inv_diag, a.work, a.y);
+  cl_load_owned(cl, n, a.y, a.work);
+  cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, a.dvec);
+
+  // x+ = x + alpha d + beta (x - x_prev) on owned rows; ||x+||^2
+  double xs = 0.0, bad = 0.0;
+  for_owned_rows(cl, n, [&](int i) {
+    const double xi = __ldcg(a.x + i), xp = __ldcg(a.x_prev + i), di = __ldcg(a.dvec + i);
+    const double xn = xi + S.alpha * di + S.beta * (xi - xp);
+    __stcg(a.x_prev + i, xi);
+    __stcg(a.x + i, xn);
+    xs += xn * xn;
+    if (!isfinite(xn)) bad = 1.0;
+  });
+  const double xn2 = cl_sum(cl, cta_sum(xs), a.slots);
+  const double anybad = cl_max(cl, cta_max(bad), a.slots);
+  if (cl.rank == 0 && threadIdx.x == 0) {
+    a.st->iter = S.iter + 1;
+    a.st->fired = fired;
+    a.st->extra_left = extra_left;
+    a.st->have_prev = 1;
+    a.st->xnorm = sqrt(xn2);
+    a.st->rnorm = rnorm;
+    a.st->dnorm = dnorm;
+    if (anybad != 0.0) {
+      a.st->nonfinite = 1; a.st->done = 1; a.st->stop_reason = 3;
+      atomicOr(a.status, LS_DEV_NONFINITE);
+    }
+  }
+}
+
+// y = R^{-T} c, d = R^{-1} y, x += d (standalone correction).
+__global__ void __launch_bounds__(256) k_correct(StepArgs a) {
+  const CL cl = cl_this();
+  const int n = a.n;
+  cl_load_owned(cl, n, a.c_in, a.work);
+  cl_solve_RT(cl, a.Rt, n, a.inv_diag, a.work, a.y);
+  cl_load_owned(cl, n, a.y, a.work);
+  cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, a.dvec);
+  for_owned_rows(cl, n, [&](int i) {
+    const double di = __ldcg(a.dvec + i);
+    __stcg(a.x + i, __ldcg(a.x + i) + di);
+    if (a.y_out) a.y_out[i] = __ldcg(a.y + i);
+    if (a.d_out) a.d_out[i] = di;
+  });
+}
+
+// ------------------------------------------------------------ host side
+PassGeom pass_geometry(const ls_ctx* ctx, int64_t n, int64_t m) {
+  PassGeom g;
+  if (n <= 256) {
+    g.boxw = (int)((n + 1) & ~1LL);
+    g.nbox = 1;
+    const int rowbytes = g.boxw * 8;
+    int tr = (48 * 1024) / rowbytes;
+    tr = (tr / 8) * 8;
+    tr = std::max(8, std::min(256, tr));
+    g.tr = tr;
+  } else {
+    g.boxw = 256;
+    g.nbox = (int)((n + 255) / 256);
+    g.tr = (g.nbox <= 4) ? 8 : 4;
+  }
+  const size_t stage = (size_t)g.tr * g.nbox * g.boxw * sizeof(double);
+  g.stages = (int)std::max<size_t>(2, std::min<size_t>(4, (200 * 1024) / stage));
+  const int64_t ntiles = (m + g.tr - 1) / g.tr;
+  g.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ntiles));
+  g.smem = g.stages * stage + (size_t)((n + 1) & ~1LL) * 8 + 2 * g.tr * 8 + (2 * kConsumerWarps + 8) * 8 +
+           2 * g.stages * 8 + 128;
+  // phase-2 group sums for n < 256 reuse the tile memory
+  return g;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t make_tensor_map(ls_ctx* ctx, CUtensorMap* map, const double* A, int64_t m, int64_t n, int64_t lda,
+                            const PassGeom& g) {
+  if (!ctx->encode_tiled) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    ctx->encode_tiled = fn;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(double)};
+  cuuint32_t box[2] = {(cuuint32_t)g.boxw, (cuuint32_t)g.tr};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = ((EncodeTiledFn)ctx->encode_tiled)(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)A, dims, strides, box,
+                                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int NPT>
+static cudaError_t launch_pass_t(ls_ctx* ctx, const CUtensorMap& map, const PassGeom& g, const PassArgs& a) {
+  cudaError_t e = cudaFuncSetAttribute(k_fused_pass<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+  if (e != cudaSuccess) return e;
+  k_fused_pass<NPT><<<g.grid, kThreads, g.smem, ctx->stream>>>(map, a);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_pass(ls_ctx* ctx, const CUtensorMap& map, const PassGeom& g, int64_t m, int64_t n,
+                              const double* b, const double* x, const double* r_prev, double* r_out, double* part,
+                              const IterState* st) {
+  PassArgs a;
+  a.m = m; a.n = (int)n; a.boxw = g.boxw; a.nbox = g.nbox; a.tr = g.tr; a.stages = g.stages;
+  a.ntiles = (int)((m + g.tr - 1) / g.tr);
+  a.b = b; a.x = x; a.r_prev = r_prev; a.r_out = r_out; a.part = part; a.st = st; a.status = ctx->d_status;
+  const int npt = (int)((n + 255) / 256);
+  if (npt <= 1) return launch_pass_t<1>(ctx, map, g, a);
+  if (npt <= 2) return launch_pass_t<2>(ctx, map, g, a);
+  if (npt <= 4) return launch_pass_t<4>(ctx, map, g, a);
+  if (npt <= 8) return launch_pass_t<8>(ctx, map, g, a);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reduce_partials(ls_ctx* ctx, const double* part, int nparts, int64_t n, double* c,
+                                   double* norms) {
+  const int threads = 256;
+  const int grid = (int)((n + 2 + threads - 1) / threads);
+  k_reduce_partials<<<grid, threads, 0, ctx->stream>>>(part, nparts, (int)n, c, norms);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iter_step(ls_ctx* ctx, const StepArgs& a) {
+  StepArgs aa = a;
+  void* args[] = {&aa};
+  return launch_cluster(ctx, (const void*)k_iter_step, args, ctx->cluster);
+}
+
+cudaError_t launch_correct(ls_ctx* ctx, const StepArgs& a) {
+  StepArgs aa = a;
+  void* args[] = {&aa};
+  return launch_cluster(ctx, (const void*)k_correct, args, ctx->cluster);
+}
+
+}  // namespace lsk

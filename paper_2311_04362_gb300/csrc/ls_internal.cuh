@@ -1,0 +1,323 @@
+// ls_internal.cuh -- shared declarations of the libls CUDA sources (sm_103a).
+//
+// Device helpers used by several kernels: the Philox4x32-10 counter hash
+// (Salmon et al., SC'11), Lemire's bounded draw, bounded-time waits on
+// mbarriers and on a grid barrier, and thin inline-PTX wrappers for TMA
+// (cp.async.bulk.tensor), mbarrier and thread-block-cluster operations.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ls.h"
+
+// ---------------------------------------------------------------- status bits
+// Written by kernels into ctx->d_status; mapped to ls_status on the host.
+#define LS_DEV_TIMEOUT 1u
+#define LS_DEV_RANK 2u
+#define LS_DEV_NONFINITE 4u
+#define LS_DEV_BADSIZE 8u
+
+// A bounded wait gives up after this many nanoseconds of %globaltimer.
+#define LS_WAIT_NS 2000000000ull
+
+namespace lsk {
+
+// --------------------------------------------------------------- Philox4x32-10
+struct u32x4 { uint32_t x, y, z, w; };
+
+__host__ __device__ inline u32x4 philox10(u32x4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    u32x4 n;
+    n.x = (uint32_t)(p1 >> 32) ^ c.y ^ k0;
+    n.y = (uint32_t)p1;
+    n.z = (uint32_t)(p0 >> 32) ^ c.w ^ k1;
+    n.w = (uint32_t)p0;
+    c = n;
+  }
+  return c;
+}
+
+// Word stream of one counter family: block t = philox(lo(idx), hi(idx), t, dom).
+struct WordStream {
+  uint32_t k0, k1, c0, c1, dom, blk;
+  uint32_t buf[4];
+  int pos;
+  __host__ __device__ WordStream(uint64_t seed, uint64_t idx, uint32_t domain)
+      : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), c0((uint32_t)idx),
+        c1((uint32_t)(idx >> 32)), dom(domain), blk(0), pos(4) {}
+  __host__ __device__ uint32_t next() {
+    if (pos == 4) {
+      u32x4 o = philox10(u32x4{c0, c1, blk, dom}, k0, k1);
+      buf[0] = o.x; buf[1] = o.y; buf[2] = o.z; buf[3] = o.w;
+      ++blk;
+      pos = 0;
+    }
+    return buf[pos++];
+  }
+  // Uniform in [0, range), range >= 1 (Lemire's multiply-shift with rejection).
+  __host__ __device__ uint32_t below(uint32_t range) {
+    uint64_t p = (uint64_t)next() * range;
+    uint32_t lo = (uint32_t)p;
+    if (lo < range) {
+      const uint32_t thr = (uint32_t)(0u - range) % range;
+      while (lo < thr) { p = (uint64_t)next() * range; lo = (uint32_t)p; }
+    }
+    return (uint32_t)(p >> 32);
+  }
+};
+
+// ------------------------------------------------------------------ timers
+__device__ inline uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// --------------------------------------------------------------- mbarrier
+__device__ inline uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ inline void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ inline void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity; false if the deadline passed.
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t deadline) {
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0 && gtimer() > deadline) return false;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------- TMA
+__device__ inline void tma_load_2d(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(smem_dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ inline void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+
+// ---------------------------------------------------------------- clusters
+__device__ inline uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ inline uint32_t cluster_nctas() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ inline void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of `p` (this CTA's shared memory) in the shared window of CTA `rank`.
+__device__ inline uint32_t map_shared(const void* p, uint32_t rank) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_u32(p)), "r"(rank));
+  return out;
+}
+__device__ inline void st_cluster_f64(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ inline double ld_cluster_f64(uint32_t addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// ------------------------------------------------------------- grid barrier
+// Sense-free generation barrier for a cooperative launch (all CTAs are
+// co-resident).  Every wait is bounded; on timeout the status word gets
+// LS_DEV_TIMEOUT and all CTAs return false from then on.
+struct GridBar {
+  unsigned int* count;   // zero-initialised
+  unsigned int* gen;
+  unsigned int* status;
+};
+
+__device__ inline bool grid_sync(const GridBar& gb, unsigned int nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = gb.gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(gb.count, 1u);
+    if (arrived == nblocks - 1) {
+      *gb.count = 0;
+      __threadfence();
+      atomicAdd(gb.gen, 1u);
+    } else {
+      const uint64_t deadline = gtimer() + LS_WAIT_NS;
+      uint32_t spins = 0;
+      while (*vgen == g) {
+        if ((++spins & 63u) == 0) {
+          if (gtimer() > deadline) { atomicOr(gb.status, LS_DEV_TIMEOUT); ok = 0; break; }
+          if (*(volatile unsigned int*)gb.status & LS_DEV_TIMEOUT) { ok = 0; break; }
+        }
+        __nanosleep(40);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------ reductions
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace lsk
+
+// -------------------------------------------------------------------- context
+struct ls_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  // device arena (grown on demand, never shrunk)
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // small persistent device buffers
+  unsigned int* d_status = nullptr;    // [0] status bits, [1..3] barrier counters
+  int* d_misc = nullptr;               // small integer scratch (max bucket size, ...)
+  // pinned host mirror for readbacks
+  void* h_pinned = nullptr;
+  // staging for host inputs of ls_solve
+  char* stage = nullptr;
+  size_t stage_bytes = 0;
+  // sort scratch for sketch rows with more than the shared-memory capacity
+  void* aux = nullptr;
+  size_t aux_bytes = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> pass_ev;    // two per fused-pass launch of ls_iterate
+  long long launches = 0;              // kernels launched (for ls_info)
+  // cluster size used by the small dense kernels
+  int cluster = 8;
+  // TMA encode entry point
+  void* encode_tiled = nullptr;
+};
+
+// ------------------------------------------------------------ launch helpers
+// Implemented in sketch.cu / factor.cu / iterate.cu; all enqueue on ctx->stream
+// and return cudaSuccess or the first launch error.
+namespace lsk {
+
+cudaError_t launch_sketch_indices(ls_ctx* ctx, int64_t m, int64_t d, int zeta, uint64_t seed,
+                                  int32_t* rows, uint32_t* signs);
+// With max_bucket_host != null: histogram + scan only, returns the largest
+// bucket (synchronises).  Otherwise histogram, scan, scatter and bucket sort.
+cudaError_t launch_sketch_csr(ls_ctx* ctx, int64_t m, int64_t d, int zeta, const int32_t* rows,
+                              const uint32_t* signs, int64_t* row_ptr, uint32_t* ent,
+                              unsigned long long* fill, uint32_t* sort_scratch, int* max_bucket_host);
+int sketch_sort_cap();
+cudaError_t launch_sketch_apply(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda,
+                                const double* b, int64_t d, const int64_t* row_ptr,
+                                const uint32_t* ent, double scale, double* B, int64_t ldb);
+
+int householder_ctas(const ls_ctx* ctx, int64_t d);
+size_t householder_part_doubles(const ls_ctx* ctx, int64_t d, int64_t n);
+cudaError_t launch_householder(ls_ctx* ctx, double* B, int64_t d, int64_t n, int64_t ldb,
+                               double* part, double* w);
+cudaError_t launch_prepare_R(ls_ctx* ctx, const double* src, int64_t lds, int64_t n, double* R_out,
+                             int64_t ldr, double* Rt, double* inv_diag);
+cudaError_t launch_post_factor(ls_ctx* ctx, const double* B, int64_t d, int64_t n, int64_t ldb,
+                               const double* R, int64_t ldr, double* x0, uint64_t seed,
+                               const double* Rt, const double* inv_diag, double* vecs /* 4n+64 */,
+                               double* est_out /* 2 */);
+cudaError_t launch_cluster(ls_ctx* ctx, const void* fn, void** args, int cluster);
+
+// Iteration state on the device.
+struct IterState {
+  int iter;          // updates applied
+  int done;          // 1: stop (rule held and extra updates done) or error
+  int fired;         // the stopping rule has held
+  int extra_left;    // updates remaining after the rule held
+  int stop_reason;   // 0 rule held, 1 q reached, 3 non-finite
+  int nonfinite;
+  int have_prev;     // r_prev holds r(x_{i-1})
+  int pad;
+  double xnorm;      // ||x_i||
+  double rnorm;      // ||r(x_i)||
+  double dnorm;      // ||r(x_i) - r(x_{i-1})||
+  double normest, condest, gamma, rho, alpha, beta;
+};
+
+struct PassGeom {
+  int boxw;      // TMA box width (columns), even, <= 256
+  int nbox;      // boxes per row
+  int tr;        // rows per tile
+  int stages;    // pipeline stages
+  size_t smem;   // dynamic shared memory bytes
+  int grid;      // CTAs (one per SM)
+};
+PassGeom pass_geometry(const ls_ctx* ctx, int64_t n, int64_t m);
+cudaError_t make_tensor_map(ls_ctx* ctx, CUtensorMap* map, const double* A, int64_t m, int64_t n,
+                            int64_t lda, const PassGeom& g);
+cudaError_t launch_fused_pass(ls_ctx* ctx, const CUtensorMap& map, const PassGeom& g, int64_t m,
+                              int64_t n, const double* b, const double* x, const double* r_prev,
+                              double* r_out, double* part, const IterState* st);
+cudaError_t launch_reduce_partials(ls_ctx* ctx, const double* part, int nparts, int64_t n,
+                                   double* c, double* norms);
+
+struct StepArgs {
+  const double* part; int nparts;
+  const double* Rt; const double* R; int64_t ldr; const double* inv_diag; int n;
+  double* x; double* x_prev;
+  double* y; double* dvec; double* work; double* slots;
+  IterState* st;
+  int use_stop; int extra;
+  unsigned int* status;
+  const double* c_in;     // k_correct: c given directly
+  double* y_out; double* d_out;
+};
+cudaError_t launch_iter_step(ls_ctx* ctx, const StepArgs& a);
+cudaError_t launch_correct(ls_ctx* ctx, const StepArgs& a);
+
+}  // namespace lsk

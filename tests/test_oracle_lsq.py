@@ -224,3 +224,15 @@ def test_zero_start_still_converges():
     fe_qr = oracle.forward_error(oracle.qr_solve(P["A"], P["b"]), P["x"])
     assert oracle.forward_error(x, P["x"]) <= 10 * fe_qr
     assert info["iters"] >= info1["iters"]
+
+
+def test_lapack_householder_solve_same_class_as_plain():
+    """The LAPACK-backed Householder solve (used for very tall problems) lands
+    in the same forward-error class as the plain-loop oracle solve."""
+    for kappa, res in [(1e8, 1e-4), (1e10, 1e-6), (1e3, 1e-10)]:
+        P = problems.make_problem(3000, 40, kappa, res, 11)
+        fe_plain = oracle.forward_error(oracle.qr_solve(P["A"], P["b"]), P["x"])
+        fe_lapack = oracle.forward_error(oracle.qr_solve_lapack(P["A"], P["b"]), P["x"])
+        wedin = 2.23 * kappa * (1.0 + kappa * res) * U
+        assert fe_lapack <= 100 * wedin
+        assert 0.05 * fe_plain <= fe_lapack <= 20 * fe_plain
