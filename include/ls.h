@@ -168,6 +168,36 @@ LS_API ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t
                    int64_t lda, int64_t d, int zeta, int q, uint64_t seed, double* x,
                    ls_info* info);
 
+/* Fused residual/gradient pass that allocates nothing (no counterpart in the
+ * paper: this is an interface for callers, not a step of the method).
+ *
+ * Some callers cannot call cudaMalloc: code that runs inside a memory pool or
+ * arena it does not own, code under a framework that forbids device
+ * allocation on its hot path, or code that must not trigger the implicit
+ * synchronisation an allocation can cause.  An ls_ctx allocates its scratch,
+ * so those callers use this entry point instead; it needs no context.
+ *
+ * Computes exactly what ls_residual_gradient computes (same kernels, same
+ * fixed summation order, so the same bits), on `cuda_stream` (a cudaStream_t,
+ * 0 = the legacy default stream) of the CURRENT device.  The caller still
+ * passes every input and output (device memory).  The per-CTA partial sums
+ * live in a fixed array inside the library, about 1.3 MB, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ * Limits: n <= 1024 (the array's size); beyond that the call returns
+ * LS_EINVAL.  Also LS_EINVAL for the argument rules of ls_residual_gradient,
+ * LS_ECUDA on a non-sm_103 device or a CUDA error, LS_ETIMEOUT if a bounded
+ * device wait gave up.  The first call on a device looks up the array's
+ * device address (set-up, once per device); make that first call before any
+ * stream capture.  All calls share the one array: calls that overlap on the
+ * GPU (concurrent streams, or several host threads) race on it and must be
+ * serialised by the caller.  Returns after the work finished (synchronises
+ * the stream). */
+LS_API ls_status ls_residual_gradient_noalloc(void* cuda_stream, const double* A, int64_t m, int64_t n,
+                                              int64_t lda, const double* b, const double* x,
+                                              const double* r_prev, double* r_out, double* c,
+                                              double* norms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,8 @@ def lib():
     L.ls_iterate.restype = S
     L.ls_solve.argtypes = [P, P, P, I64, I64, I64, I64, I, I, C.c_uint64, P, C.POINTER(ls_info)]
     L.ls_solve.restype = S
+    L.ls_residual_gradient_noalloc.argtypes = [P, P, I64, I64, I64, P, P, P, P, P, P]
+    L.ls_residual_gradient_noalloc.restype = S
     _lib = L
     return L
 
