@@ -41,14 +41,21 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # ncu DRAM traffic (read + write bytes) of one fused-pass launch on this workload,
 # keyed by the sha256 of the kernel source it was taken on; stale -> null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"18953f771f25a885": 16.078e9}   # profiles/fused_pass_m200000_n1000.md, x10 rows
 
 
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for f in ["iterate.cu", "cluster_la.cuh", "ls_internal.cuh"]:
-        with open(os.path.join(ROOT, "paper_2311_04362_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    """Hash of the fused-pass kernel's source (its function body in iterate.cu
+    plus the device helpers it uses)."""
+    csrc = os.path.join(ROOT, "paper_2311_04362_gb300", "csrc")
+    with open(os.path.join(csrc, "iterate.cu")) as fh:
+        text = fh.read()
+    start = text.index("struct PassArgs {")
+    end = text.index("// Sum the per-CTA partials in CTA order")
+    h = hashlib.sha256(text[start:end].encode())
+    with open(os.path.join(csrc, "ls_internal.cuh")) as fh:
+        helpers = fh.read()
+    h.update(helpers[:helpers.index("// -------------------------------------------------------------------- context")].encode())
     return h.hexdigest()[:16]
 
 

@@ -164,7 +164,7 @@ struct FactorScratch {
 FactorScratch carve_factor(Carve& c, const ls_ctx* ctx, int64_t d, int64_t n) {
   FactorScratch f;
   f.part = c.take<double>(householder_part_doubles(ctx, d, n));
-  f.w = c.take<double>((size_t)n + 2);
+  f.w = c.take<double>(householder_w_doubles(n));
   f.Rt = c.take<double>((size_t)n * n);
   f.inv_diag = c.take<double>((size_t)n);
   f.vecs = c.take<double>(4 * (size_t)n + 64);

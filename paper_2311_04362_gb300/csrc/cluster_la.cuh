@@ -157,13 +157,20 @@ __device__ inline void cl_solve_RT(const CL& cl, const double* __restrict__ Rt, 
   for (int b = 0; b < nb; ++b) {
     const int r0 = 32 * b, bs = min(32, n - r0);
     if ((uint32_t)(b % (int)cl.ncta) == cl.rank && threadIdx.x < 32) {
+      // lane l holds row l of the diagonal block of R^T (one wave of loads)
       const int l = threadIdx.x;
+      double rowv[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        rowv[i] = (l < bs && i < l) ? __ldg(Rt + (size_t)(r0 + l) + (size_t)(r0 + i) * n) : 0.0;
+      const double inv = (l < bs) ? __ldg(inv_diag + r0 + l) : 0.0;
       double wl = (l < bs) ? __ldcg(work + r0 + l) : 0.0;
       double yl = 0.0;
-      for (int i = 0; i < bs; ++i) {
-        const double yi = __shfl_sync(0xffffffffu, wl, i) * __ldg(inv_diag + r0 + i);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const double yi = __shfl_sync(0xffffffffu, wl * inv, i);
         if (l == i) yl = yi;
-        if (l > i && l < bs) wl = wl - __ldg(Rt + (size_t)(r0 + l) + (size_t)(r0 + i) * n) * yi;
+        if (l > i) wl = wl - rowv[i] * yi;
       }
       if (l < bs) __stcg(y + r0 + l, yl);
     }
@@ -173,7 +180,9 @@ __device__ inline void cl_solve_RT(const CL& cl, const double* __restrict__ Rt, 
     for_owned_rows(cl, n, [&](int i) {
       if (i >= r0 + 32) {
         double s = 0.0;
-        for (int k = 0; k < bs; ++k) s += __ldg(Rt + (size_t)i + (size_t)(r0 + k) * n) * yb[k];
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (k < bs) s += __ldg(Rt + (size_t)i + (size_t)(r0 + k) * n) * yb[k];
         __stcg(work + i, __ldcg(work + i) - s);
       }
     });
@@ -191,13 +200,20 @@ __device__ inline void cl_solve_R(const CL& cl, const double* __restrict__ R, in
   for (int b = nb - 1; b >= 0; --b) {
     const int r0 = 32 * b, bs = min(32, n - r0);
     if ((uint32_t)(b % (int)cl.ncta) == cl.rank && threadIdx.x < 32) {
+      // lane l holds row l of the diagonal block of R (one wave of loads)
       const int l = threadIdx.x;
+      double rowv[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        rowv[i] = (l < bs && i > l && i < bs) ? __ldg(R + (size_t)(r0 + l) + (size_t)(r0 + i) * ldr) : 0.0;
+      const double inv = (l < bs) ? __ldg(inv_diag + r0 + l) : 0.0;
       double wl = (l < bs) ? __ldcg(work + r0 + l) : 0.0;
       double xl = 0.0;
-      for (int i = bs - 1; i >= 0; --i) {
-        const double xi = __shfl_sync(0xffffffffu, wl, i) * __ldg(inv_diag + r0 + i);
+#pragma unroll
+      for (int i = 31; i >= 0; --i) {
+        const double xi = __shfl_sync(0xffffffffu, wl * inv, i);
         if (l == i) xl = xi;
-        if (l < i) wl = wl - __ldg(R + (size_t)(r0 + l) + (size_t)(r0 + i) * ldr) * xi;
+        if (l < i) wl = wl - rowv[i] * xi;
       }
       if (l < bs) __stcg(x + r0 + l, xl);
     }
@@ -207,7 +223,9 @@ __device__ inline void cl_solve_R(const CL& cl, const double* __restrict__ R, in
     for_owned_rows(cl, n, [&](int i) {
       if (i < r0) {
         double s = 0.0;
-        for (int k = 0; k < bs; ++k) s += __ldg(R + (size_t)i + (size_t)(r0 + k) * ldr) * xb[k];
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (k < bs) s += __ldg(R + (size_t)i + (size_t)(r0 + k) * ldr) * xb[k];
         __stcg(work + i, __ldcg(work + i) - s);
       }
     });

@@ -20,6 +20,8 @@
 // k_post_factor: one thread-block cluster.  Solves R x0 = (Q^T S b)[0:n],
 // runs ceil(ln n) power steps on R (normest) and Hager's 1-norm estimator of
 // ||R^{-1}||_1 times ||R||_1 (condest).
+#include <algorithm>
+
 #include "cluster_la.cuh"
 
 namespace lsk {
@@ -124,6 +126,240 @@ __global__ void __launch_bounds__(256) k_householder(double* __restrict__ B, int
       }
     }
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ blocked QR
+// k_householder_blocked: the same reflectors, applied panel by panel
+// (Schreiber-Van Loan compact WY).  For each panel of kNB columns:
+//   * the panel slice of this CTA's rows is factored in shared memory, one
+//     column at a time (two grid barriers per column: norm partials, then dot
+//     partials), exactly the unblocked steps restricted to the panel;
+//   * T (kNB x kNB, upper triangular) from G = V^T V: T[b][b] = tau_b,
+//     T[0:b, b] = -tau_b T[0:b, 0:b] G[0:b, b];
+//   * the trailing columns (including S b) get C <- C - V (T^T (V^T C)):
+//     W = V^T C as per-CTA partials summed in CTA order, W' = T^T W, then
+//     every CTA updates its own rows.  Both products run thread-per-column
+//     with kNB FP64 accumulators in registers and V broadcast from shared
+//     memory.
+static constexpr int kNB = 32;
+
+struct HhArgs {
+  double* B; int64_t d; int n; int64_t ldb;
+  double* part;   // householder_part_doubles()
+  double* Wp;     // kNB * (n + 1)
+  GridBar gb;
+};
+
+__device__ inline int panel_ld(int64_t ch) { return (int)(ch + 1 + (ch & 1)); }   // odd stride
+
+__global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
+  extern __shared__ double sm[];
+  __shared__ double s_tau[kNB], s_beta[kNB];
+  __shared__ double s_par[3];
+  __shared__ int s_bad;
+  const int P = gridDim.x, p = blockIdx.x;
+  const int n = a.n, ncols = n + 1;
+  const int64_t ch = (a.d + P - 1) / P;
+  const int64_t r0 = (int64_t)p * ch;
+  const int64_t r1 = min(a.d, r0 + ch);
+  const int nrow = (int)max((int64_t)0, r1 - r0);
+  const int ldp = panel_ld(ch);
+  double* Ps = sm;                           // kNB columns x ldp (column-major)
+  double* Ts = Ps + (size_t)kNB * ldp;       // T, row-major kNB x kNB
+  double* Gs = Ts + kNB * kNB;               // G, row-major kNB x kNB
+  double* pnorm = a.part;                    // [P]
+  double* alpha_slot = a.part + P;           // [1]
+  double* pdot = a.part + P + 8;             // [P][kNB]
+  double* pW = pdot + (size_t)P * kNB;       // [P][kNB][ncols]
+  double* pG = pW + (size_t)P * kNB * ncols; // [P][kNB*kNB]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  double* B = a.B;
+  const int64_t ldb = a.ldb;
+
+  // norm partial of panel column kk (global column k) over own rows > k; owner publishes alpha
+  auto norm_partial = [&](int kk, int k) {
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < nrow; i += blockDim.x)
+      if (r0 + i > k) { const double v = Ps[kk * ldp + i]; ss += v * v; }
+    ss = cta_sum(ss);
+    if (threadIdx.x == 0) {
+      __stcg(pnorm + p, ss);
+      if (k >= r0 && k < r1) __stcg(alpha_slot, Ps[kk * ldp + (k - r0)]);
+    }
+  };
+
+  for (int k0 = 0; k0 < n; k0 += kNB) {
+    const int nbp = min(kNB, n - k0);
+    for (int e = threadIdx.x; e < kNB * nrow; e += blockDim.x) {
+      const int c = e / nrow, i = e - c * nrow;
+      Ps[c * ldp + i] = (c < nbp) ? B[(r0 + i) + (int64_t)(k0 + c) * ldb] : 0.0;
+    }
+    __syncthreads();
+    norm_partial(0, k0);
+
+    // ---------------------------------------------------- panel factorization
+    for (int kk = 0; kk < nbp; ++kk) {
+      const int k = k0 + kk;
+      if (!grid_sync(a.gb, P)) return;
+      if (warp == 0) {
+        double t = 0.0;
+        for (int q = lane; q < P; q += 32) t += __ldcg(pnorm + q);
+        t = warp_sum(t);
+        if (lane == 0) {
+          const double alpha = __ldcg(alpha_slot);
+          const double xnorm = sqrt(t);
+          double beta, tau, scal;
+          if (xnorm == 0.0) {
+            beta = alpha; tau = 0.0; scal = 1.0;
+          } else {
+            const double h = hypot(alpha, xnorm);
+            beta = (alpha >= 0.0) ? -h : h;
+            tau = (beta - alpha) / beta;
+            scal = 1.0 / (alpha - beta);
+          }
+          s_par[0] = beta; s_par[1] = tau; s_par[2] = scal;
+          s_tau[kk] = tau; s_beta[kk] = beta;
+          s_bad = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+        }
+      }
+      __syncthreads();
+      if (s_bad) {
+        if (p == 0 && threadIdx.x == 0) atomicOr(a.gb.status, LS_DEV_RANK);
+        return;
+      }
+      const double tau = s_par[1], scal = s_par[2];
+      for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+        const int64_t g = r0 + i;
+        if (g == k) Ps[kk * ldp + i] = 1.0;
+        else if (g > k && tau != 0.0) Ps[kk * ldp + i] *= scal;
+      }
+      __syncthreads();
+      if (kk + 1 < nbp) {
+        // dots of v with the remaining panel columns (own rows >= k)
+        const int i0 = (int)max((int64_t)0, (int64_t)k - r0);
+        for (int jj = kk + 1 + warp; jj < nbp; jj += nwarp) {
+          double s = 0.0;
+          if (tau != 0.0)
+            for (int i = i0 + lane; i < nrow; i += 32) s += Ps[kk * ldp + i] * Ps[jj * ldp + i];
+          s = warp_sum(s);
+          if (lane == 0) __stcg(pdot + (size_t)p * kNB + jj, s);
+        }
+        if (!grid_sync(a.gb, P)) return;
+        __shared__ double s_w[kNB];
+        for (int jj = kk + 1 + warp; jj < nbp; jj += nwarp) {
+          double s = 0.0;
+          for (int q = lane; q < P; q += 32) s += __ldcg(pdot + (size_t)q * kNB + jj);
+          s = warp_sum(s);
+          if (lane == 0) s_w[jj] = s;
+        }
+        __syncthreads();
+        if (tau != 0.0) {
+          for (int e = threadIdx.x; e < (nbp - kk - 1) * nrow; e += blockDim.x) {
+            const int jj = kk + 1 + e / nrow, i = e % nrow;
+            if (r0 + i >= k) Ps[jj * ldp + i] -= (tau * s_w[jj]) * Ps[kk * ldp + i];
+          }
+        }
+        __syncthreads();
+        norm_partial(kk + 1, k + 1);
+      }
+    }
+
+    // ---------------------------------------------------- write back, form V
+    for (int e = threadIdx.x; e < nbp * nrow; e += blockDim.x) {
+      const int c = e / nrow, i = e - c * nrow;
+      const int64_t g = r0 + i;
+      const double v = Ps[c * ldp + i];
+      B[g + (int64_t)(k0 + c) * ldb] = (g == k0 + c) ? s_beta[c] : v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kNB * nrow; e += blockDim.x) {
+      const int c = e / nrow, i = e - c * nrow;
+      const int64_t g = r0 + i;
+      if (c >= nbp || g < k0 + c) Ps[c * ldp + i] = 0.0;
+      else if (g == k0 + c) Ps[c * ldp + i] = 1.0;
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------- partial G and W = V^T C
+    const int i0 = (int)max((int64_t)0, (int64_t)k0 - r0);
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+      const int r = e / kNB, c = e - r * kNB;
+      double s = 0.0;
+      if (r < c && c < nbp)
+        for (int i = i0; i < nrow; ++i) s += Ps[r * ldp + i] * Ps[c * ldp + i];
+      __stcg(pG + (size_t)p * kNB * kNB + e, s);
+    }
+    const int jt0 = k0 + nbp;
+    for (int j = jt0 + threadIdx.x; j < ncols; j += blockDim.x) {
+      double acc[kNB];
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) acc[q] = 0.0;
+      const double* cp = B + (int64_t)j * ldb + r0;
+      for (int i = i0; i < nrow; ++i) {
+        const double c = cp[i];
+#pragma unroll
+        for (int q = 0; q < kNB; ++q) acc[q] += Ps[q * ldp + i] * c;
+      }
+      double* out = pW + (size_t)p * kNB * ncols + j;
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) __stcg(out + (size_t)q * ncols, acc[q]);
+    }
+    if (!grid_sync(a.gb, P)) return;
+
+    // ---------------------------------------------------- T (every CTA), W' = T^T W
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+      double s = 0.0;
+      for (int q = 0; q < P; ++q) s += __ldcg(pG + (size_t)q * kNB * kNB + e);
+      Gs[e] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int r = lane;
+      for (int c = 0; c < kNB; ++c) {
+        double t = 0.0;
+        if (c < nbp) {
+          if (r == c) t = s_tau[c];
+          else if (r < c) {
+            double s = 0.0;
+            for (int q = r; q < c; ++q) s += Ts[r * kNB + q] * Gs[q * kNB + c];
+            t = -s_tau[c] * s;
+          }
+        }
+        Ts[r * kNB + c] = t;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int j = jt0 + p * nwarp + warp; j < ncols; j += P * nwarp) {
+      double w = 0.0;
+      for (int q = 0; q < P; ++q) w += __ldcg(pW + ((size_t)q * kNB + lane) * ncols + j);
+      double wp = 0.0;
+      for (int b = 0; b < kNB; ++b) {
+        const double wb = __shfl_sync(0xffffffffu, w, b);
+        if (b <= lane) wp += Ts[b * kNB + lane] * wb;
+      }
+      __stcg(a.Wp + (size_t)lane * ncols + j, wp);
+    }
+    if (!grid_sync(a.gb, P)) return;
+
+    // ---------------------------------------------------- C -= V W' on own rows
+    for (int j = jt0 + threadIdx.x; j < ncols; j += blockDim.x) {
+      double wv[kNB];
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) wv[q] = __ldcg(a.Wp + (size_t)q * ncols + j);
+      double* cp = B + (int64_t)j * ldb + r0;
+      for (int i = i0; i < nrow; ++i) {
+        double c = cp[i];
+#pragma unroll
+        for (int q = 0; q < kNB; ++q) c -= Ps[q * ldp + i] * wv[q];
+        cp[i] = c;
+      }
+    }
+    __syncthreads();
+    if (k0 + kNB < n) {
+      // the next panel's first column was just updated by this CTA
+    }
   }
 }
 
@@ -306,18 +542,36 @@ int householder_ctas(const ls_ctx* ctx, int64_t d) {
   return (int)p;
 }
 
+static constexpr int64_t kBlockedMaxChunk = 600;   // panel slice rows per CTA in shared memory
+
+static size_t blocked_smem(int64_t ch) {
+  const int64_t ldp = ch + 1 + (ch & 1);
+  return (size_t)(kNB * ldp + 2 * kNB * kNB) * sizeof(double);
+}
+
 cudaError_t launch_householder(ls_ctx* ctx, double* B, int64_t d, int64_t n, int64_t ldb, double* part,
                                double* w) {
   const int P = householder_ctas(ctx, d);
   const int64_t chunk = (d + P - 1) / P;
-  const size_t smem = (size_t)chunk * sizeof(double);
   cudaError_t e;
+  if ((e = cudaMemsetAsync(ctx->d_status + 1, 0, 2 * sizeof(unsigned int), ctx->stream)) != cudaSuccess) return e;
+  GridBar gb{ctx->d_status + 1, ctx->d_status + 2, ctx->d_status};
+  if (chunk <= kBlockedMaxChunk && n >= 2) {
+    const size_t smem = blocked_smem(chunk);
+    if ((e = cudaFuncSetAttribute(k_householder_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    HhArgs ha{B, d, (int)n, ldb, part, w, gb};
+    void* args[] = {&ha};
+    ++ctx->launches;
+    return cudaLaunchCooperativeKernel((const void*)k_householder_blocked, dim3(P), dim3(256), args, smem,
+                                       ctx->stream);
+  }
+  const size_t smem = (size_t)chunk * sizeof(double);
   if (smem > 48 * 1024) {
     if ((e = cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
   }
-  if ((e = cudaMemsetAsync(ctx->d_status + 1, 0, 2 * sizeof(unsigned int), ctx->stream)) != cudaSuccess) return e;
-  GridBar gb{ctx->d_status + 1, ctx->d_status + 2, ctx->d_status};
   int nn = (int)n;
   void* args[] = {&B, &d, &nn, &ldb, &part, &w, &gb};
   ++ctx->launches;
@@ -325,8 +579,13 @@ cudaError_t launch_householder(ls_ctx* ctx, double* B, int64_t d, int64_t n, int
 }
 
 size_t householder_part_doubles(const ls_ctx* ctx, int64_t d, int64_t n) {
-  return (size_t)householder_ctas(ctx, d) * (size_t)(n + 2) + 1;
+  const size_t P = (size_t)householder_ctas(ctx, d);
+  const size_t unblocked = P * (size_t)(n + 2) + 1;
+  const size_t blocked = P + 8 + P * kNB + P * kNB * (size_t)(n + 1) + P * kNB * kNB;
+  return std::max(unblocked, blocked);
 }
+
+size_t householder_w_doubles(int64_t n) { return (size_t)kNB * (size_t)(n + 1) + 8; }
 
 cudaError_t launch_cluster(ls_ctx* ctx, const void* fn, void** args, int cluster) {
   cudaLaunchConfig_t cfg = {};

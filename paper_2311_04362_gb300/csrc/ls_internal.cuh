@@ -263,6 +263,7 @@ cudaError_t launch_sketch_apply(ls_ctx* ctx, const double* A, int64_t m, int64_t
 
 int householder_ctas(const ls_ctx* ctx, int64_t d);
 size_t householder_part_doubles(const ls_ctx* ctx, int64_t d, int64_t n);
+size_t householder_w_doubles(int64_t n);
 cudaError_t launch_householder(ls_ctx* ctx, double* B, int64_t d, int64_t n, int64_t ldb,
                                double* part, double* w);
 cudaError_t launch_prepare_R(ls_ctx* ctx, const double* src, int64_t lds, int64_t n, double* R_out,
