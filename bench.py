@@ -333,10 +333,11 @@ def main():
 
 
 def pass_case(args):
-    """Fused residual/gradient pass alone (ls_residual_gradient) on an
-    m x 1000 row-major A (default m = 200,000: 1.6 GB, larger than L2):
-    warm-up passes, then timed passes with CUDA events on the launching
-    stream.  Used for small-case ncu captures of k_fused_pass."""
+    """Fused residual/gradient passes on an m x 1000 row-major A (default
+    m = 200,000: 1.6 GB, larger than L2) inside ls_iterate (R = s I, a stable
+    Richardson step, stopping rule off).  Each pass is timed by CUDA events
+    on its stream inside the library.  Used for small-case ncu captures of
+    k_fused_pass."""
     import torch
 
     import paper_2311_04362_gb300 as ls
@@ -348,25 +349,18 @@ def pass_case(args):
     g.manual_seed(0)
     A = torch.randn(m, n, dtype=torch.float64, device="cuda", generator=g)
     b = torch.randn(m, dtype=torch.float64, device="cuda", generator=g)
-    x = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
-    r = torch.zeros(m, dtype=torch.float64, device="cuda")
-    c = torch.empty(n, dtype=torch.float64, device="cuda")
-    norms = torch.empty(2, dtype=torch.float64, device="cuda")
+    R = torch.eye(n, dtype=torch.float64, device="cuda") * (m ** 0.5 + n ** 0.5 + 1.0)
     stream = torch.cuda.current_stream()
+    opts = ls.default_opts()
+    opts.use_stop = 0
     with ls.Context(0, stream) as ctx:
-        for _ in range(args.warmup):
-            ctx.ls_residual_gradient(A, m, n, n, b, x, r, r, c, norms)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            ctx.ls_residual_gradient(A, m, n, n, b, x, r, r, c, norms)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"case": "fused pass", "m": m, "n": n, "ms_per_call": ms,
-                      "tflops": 4.0 * m * n / (ms / 1e3) / 1e12,
-                      "gbs": 8.0 * m * (n + 3) / (ms / 1e3) / 1e9}))
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        info = ls.ls_info()
+        info.normest, info.condest = 1.0, 1.0
+        ctx.ls_iterate(A, m, n, n, b, R, n, x, args.warmup + args.steps, opts, info)
+    ms = info.ms_pass / max(1, info.n_pass)
+    print(json.dumps({"case": "fused pass in ls_iterate", "m": m, "n": n, "ms_per_pass": ms, "passes": info.n_pass,
+                      "tflops": 4.0 * m * n / (ms / 1e3) / 1e12, "gbs": 8.0 * m * (n + 3) / (ms / 1e3) / 1e9}))
 
 
 def reference_arm(args, world, rank):
