@@ -189,8 +189,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check-qr", action="store_true", help="also compute the Householder-QR forward error (slow)")
-    ap.add_argument("--case", choices=["solve", "pass"], default="solve",
-                    help="pass: only the fused residual/gradient pass on an m x 1000 problem (for ncu captures)")
+    ap.add_argument("--case", choices=["solve", "pass", "sketch"], default="solve",
+                    help="pass / sketch: only the fused residual/gradient pass, or only the sketch B = S[A b], "
+                         "on an m x 1000 problem (for ncu captures)")
     ap.add_argument("--m", type=int, default=200_000, help="rows for --case pass")
     args = ap.parse_args()
 
@@ -202,6 +203,8 @@ def main():
         return reference_arm(args, world, rank)
     if args.case == "pass":
         return pass_case(args)
+    if args.case == "sketch":
+        return sketch_case(args)
 
     import numpy as np
     import torch
@@ -361,6 +364,38 @@ def pass_case(args):
     ms = info.ms_pass / max(1, info.n_pass)
     print(json.dumps({"case": "fused pass in ls_iterate", "m": m, "n": n, "ms_per_pass": ms, "passes": info.n_pass,
                       "tflops": 4.0 * m * n / (ms / 1e3) / 1e12, "gbs": 8.0 * m * (n + 3) / (ms / 1e3) / 1e9}))
+
+
+def sketch_case(args):
+    """The sketch B = S [A b] alone (ls_sketch) on an m x 1000 row-major A
+    (default m = 200,000: 1.6 GB) with d = 20,000, zeta = 8, timed with CUDA
+    events on the launching stream.  Used for small-case ncu captures."""
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    from paper_2311_04362_gb300 import build
+
+    build.build()
+    m, n, d, zeta = args.m, 1000, 20_000, 8
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    A = torch.randn(m, n, dtype=torch.float64, device="cuda", generator=g)
+    b = torch.randn(m, dtype=torch.float64, device="cuda", generator=g)
+    B = torch.empty((n + 1) * d, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    with ls.Context(0, stream) as ctx:
+        for _ in range(args.warmup):
+            ctx.ls_sketch(A, m, n, n, b, d, zeta, 0, B, d)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.ls_sketch(A, m, n, n, b, d, zeta, 0, B, d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"case": "sketch", "m": m, "n": n, "d": d, "zeta": zeta, "ms_per_call": ms,
+                      "alg_gbs": (8.0 * m * (n + 1) + 8.0 * d * (n + 1)) / (ms / 1e3) / 1e9}))
 
 
 def reference_arm(args, world, rank):
