@@ -188,6 +188,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the damping / momentum timings")
     ap.add_argument("--check-qr", action="store_true", help="also compute the Householder-QR forward error (slow)")
     ap.add_argument("--case", choices=["solve", "pass", "sketch"], default="solve",
                     help="pass / sketch: only the fused residual/gradient pass, or only the sketch B = S[A b], "
@@ -292,6 +293,27 @@ def main():
                "fe": float(np.linalg.norm(xh.numpy() - xtrue.cpu().numpy()) / np.linalg.norm(xtrue.cpu().numpy()))}
         del Ah, bh
 
+    # App. B variants on the same problem (reported beside the Algorithm 2 headline)
+    variants = {}
+    if not args.no_variants:
+        for vname, vopts in (("damping", ls.damping_opts(n, d)), ("momentum", ls.momentum_opts(n, d))):
+            xv = torch.empty(n, dtype=torch.float64, device="cuda")
+            ctx.ls_solve_ex(A, b, m, n, n, d, zeta, q, seed, vopts, xv)   # warm
+            barrier()
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            vinfo = None
+            for _ in range(args.steps):
+                st_v, vinfo = ctx.ls_solve_ex(A, b, m, n, n, d, zeta, q, seed, vopts, xv)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vms = max_over_ranks(v0.elapsed_time(v1), pg, "cuda")
+            variants[vname] = {"value": job_throughput(world, args.steps, vms), "unit": UNIT,
+                               "iters": vinfo.iters, "alpha": vopts.alpha, "beta": vopts.beta,
+                               "fe": float(torch.linalg.norm(xv - xtrue) / torch.linalg.norm(xtrue)),
+                               "status": ls.STATUS_NAMES[st_v]}
+
     fe_qr = None
     if args.check_qr and rank == 0:
         import oracle
@@ -323,6 +345,7 @@ def main():
                          "kernel_source_hash": khash},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "accuracy": {"fe": fe, "status": statuses, "iters": iters, **(fe_qr or {})},
+            "variants_app_b": variants,
             "phase_ms": {"sketch": statistics.mean(i.ms_sketch for _, i in infos),
                          "factor": statistics.mean(i.ms_factor for _, i in infos),
                          "iterate": statistics.mean(i.ms_iterate for _, i in infos)},

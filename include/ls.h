@@ -160,6 +160,13 @@ LS_API ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, 
                      const double* b, const double* R, int64_t ldr, double* x, int q,
                      const ls_opts* opts, ls_info* info);
 
+/* App. B, Eqs. (B.2) and (B.3): set opts->alpha / opts->beta for iterative
+ * sketching with damping (alpha = (1-e^2)^2/(1+e^2), beta = 0) or with
+ * momentum (alpha = (1-e^2)^2, beta = e^2), with the paper's recommended
+ * distortion estimate e = sqrt(n/d).  Other fields are left as they are. */
+LS_API void ls_opts_damping(ls_opts* opts, int64_t n, int64_t d);
+LS_API void ls_opts_momentum(ls_opts* opts, int64_t n, int64_t d);
+
 /* The whole method: sketch, factor, start, iterate (q <= 0 means 100).
  * A, b and x may be HOST or DEVICE pointers (detected per pointer); host
  * arrays are copied to context-owned device memory and x is copied back.
@@ -167,6 +174,12 @@ LS_API ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, 
 LS_API ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n,
                    int64_t lda, int64_t d, int zeta, int q, uint64_t seed, double* x,
                    ls_info* info);
+
+/* ls_solve with iteration options (stopping rule constants, extra updates,
+ * damping / momentum of App. B); opts may be NULL for the defaults. */
+LS_API ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n,
+                             int64_t lda, int64_t d, int zeta, int q, uint64_t seed,
+                             const ls_opts* opts, double* x, ls_info* info);
 
 /* Fused residual/gradient pass that allocates nothing (no counterpart in the
  * paper: this is an interface for callers, not a step of the method).

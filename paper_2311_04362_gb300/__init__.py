@@ -80,6 +80,11 @@ def lib():
     L.ls_iterate.restype = S
     L.ls_solve.argtypes = [P, P, P, I64, I64, I64, I64, I, I, C.c_uint64, P, C.POINTER(ls_info)]
     L.ls_solve.restype = S
+    L.ls_solve_ex.argtypes = [P, P, P, I64, I64, I64, I64, I, I, C.c_uint64, C.POINTER(ls_opts), P,
+                              C.POINTER(ls_info)]
+    L.ls_solve_ex.restype = S
+    L.ls_opts_damping.argtypes = [C.POINTER(ls_opts), I64, I64]
+    L.ls_opts_momentum.argtypes = [C.POINTER(ls_opts), I64, I64]
     L.ls_residual_gradient_noalloc.argtypes = [P, P, I64, I64, I64, P, P, P, P, P, P]
     L.ls_residual_gradient_noalloc.restype = S
     _lib = L
@@ -102,6 +107,20 @@ def _ptr(t):
 def default_opts() -> ls_opts:
     o = ls_opts()
     lib().ls_default_opts(C.byref(o))
+    return o
+
+
+def damping_opts(n: int, d: int) -> ls_opts:
+    """Defaults with the damping weights of App. B, Eq. (B.2), e = sqrt(n/d)."""
+    o = default_opts()
+    lib().ls_opts_damping(C.byref(o), n, d)
+    return o
+
+
+def momentum_opts(n: int, d: int) -> ls_opts:
+    """Defaults with the momentum weights of App. B, Eq. (B.3), e = sqrt(n/d)."""
+    o = default_opts()
+    lib().ls_opts_momentum(C.byref(o), n, d)
     return o
 
 
@@ -174,6 +193,13 @@ class Context:
         info = info if info is not None else ls_info()
         st = lib().ls_iterate(self._h, _ptr(A), m, n, lda, _ptr(b), _ptr(R), ldr, _ptr(x), q,
                               C.byref(opts) if opts is not None else None, C.byref(info))
+        self._check(st, allow=(LS_OK, LS_ENOTCONV))
+        return st, info
+
+    def ls_solve_ex(self, A, b, m, n, lda, d, zeta, q, seed, opts, x, info=None):
+        info = info if info is not None else ls_info()
+        st = lib().ls_solve_ex(self._h, _ptr(A), _ptr(b), m, n, lda, d, zeta, q, seed,
+                               C.byref(opts) if opts is not None else None, _ptr(x), C.byref(info))
         self._check(st, allow=(LS_OK, LS_ENOTCONV))
         return st, info
 

@@ -206,6 +206,20 @@ void ls_default_opts(ls_opts* o) {
   o->beta = 0.0;
 }
 
+void ls_opts_damping(ls_opts* o, int64_t n, int64_t d) {
+  if (!o || n < 1 || d < 1) return;
+  const double e2 = (double)n / (double)d;   // e = sqrt(n/d)
+  o->alpha = (1.0 - e2) * (1.0 - e2) / (1.0 + e2);
+  o->beta = 0.0;
+}
+
+void ls_opts_momentum(ls_opts* o, int64_t n, int64_t d) {
+  if (!o || n < 1 || d < 1) return;
+  const double e2 = (double)n / (double)d;
+  o->alpha = (1.0 - e2) * (1.0 - e2);
+  o->beta = e2;
+}
+
 ls_status ls_create(ls_ctx** out, int device, void* cuda_stream) {
   if (!out) return LS_EINVAL;
   *out = nullptr;
@@ -565,6 +579,11 @@ ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
 
 ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n, int64_t lda, int64_t d,
                    int zeta, int q, uint64_t seed, double* x, ls_info* info) {
+  return ls_solve_ex(ctx, A, b, m, n, lda, d, zeta, q, seed, nullptr, x, info);
+}
+
+ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n, int64_t lda, int64_t d,
+                      int zeta, int q, uint64_t seed, const ls_opts* opts, double* x, ls_info* info) {
   if (!ctx) return LS_EINVAL;
   ctx->err.clear();
   ls_status st;
@@ -631,7 +650,7 @@ ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t m, int
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
   cc.off = mark2;
   ls_info local{};
-  ls_status it = iterate_impl(ctx, Ad, m, n, lda, bd, R, n, xd, q, nullptr, est[0], est[1], cc, &local);
+  ls_status it = iterate_impl(ctx, Ad, m, n, lda, bd, R, n, xd, q, opts, est[0], est[1], cc, &local);
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], ctx->stream));
   if (it != LS_OK && it != LS_ENOTCONV) return it;
   if (!dx) CUDA_TRY(ctx, cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));

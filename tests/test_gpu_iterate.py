@@ -208,3 +208,41 @@ def test_invalid_arguments(env):
         ctx.ls_solve(A, b, 10, 4, 4, 20, 33, 10, 0, x)      # zeta > 32
     with pytest.raises(ls.LsError):
         ctx.ls_solve(A, b, 3, 4, 4, 20, 8, 10, 0, x)        # n > m
+
+
+@pytest.mark.parametrize("variant", ["damping", "momentum"])
+def test_damping_momentum_fixed_steps_match_oracle(env, variant):
+    """App. B, Eq. (B.1) update x+ = x + alpha d + beta (x - x_prev) with the
+    Eq. (B.2) / (B.3) weights, against the oracle's same update."""
+    torch, ls, ctx = env
+    P = problems.make_problem(4000, 50, 1e6, 1e-4, 8)
+    Bo = oracle.sketch(P["A"], P["b"], 1000, 8, 0)
+    R, x0, info = _factor_on_gpu(torch, ctx, Bo)
+    Rh = host(R).reshape(50, 50).T
+    opts = ls.damping_opts(50, 1000) if variant == "damping" else ls.momentum_opts(50, 1000)
+    opts.use_stop = 0
+    x = x0.clone()
+    ctx.ls_iterate(dev(torch, P["A"]), 4000, 50, 50, dev(torch, P["b"]), R, 50, x, 6, opts, info)
+    xo, _ = oracle.iterate(P["A"], P["b"], Rh, host(x0), 6, info.normest, info.condest, use_stop=False,
+                           alpha=opts.alpha, beta=opts.beta)
+    tol = 100 * 1e6 * (1 + 1e6 * 1e-4) * U
+    assert np.linalg.norm(host(x) - xo) <= tol * np.linalg.norm(xo)
+
+
+def test_damping_momentum_solve_faster_and_accurate(env):
+    """Whole solve with the stopping rule: both variants meet the forward-error
+    rule and need fewer updates than Algorithm 2 (App. B: faster rate)."""
+    torch, ls, ctx = env
+    P = problems.make_problem(4000, 50, 1e10, 1e-6, 0)
+    Ad, bd = dev(torch, P["A"]), dev(torch, P["b"])
+    fe_qr = oracle.forward_error(oracle.qr_solve(P["A"], P["b"]), P["x"])
+    iters = {}
+    for name, opts in [("basic", ls.default_opts()), ("damping", ls.damping_opts(50, 1000)),
+                       ("momentum", ls.momentum_opts(50, 1000))]:
+        x = torch.empty(50, dtype=torch.float64, device="cuda")
+        st, info = ctx.ls_solve_ex(Ad, bd, 4000, 50, 50, 1000, 8, 100, 0, opts, x)
+        assert st == ls.LS_OK
+        assert oracle.forward_error(host(x), P["x"]) <= 10 * fe_qr
+        iters[name] = info.iters
+    assert iters["momentum"] < iters["basic"]
+    assert iters["damping"] < iters["basic"]

@@ -22,7 +22,7 @@ def libpath():
 
 def test_header_declares_the_boundary():
     syms = declared_symbols()
-    for s in ["ls_create", "ls_destroy", "ls_last_error", "ls_workspace_bytes", "ls_sketch_indices",
+    for s in ["ls_create", "ls_destroy", "ls_last_error", "ls_workspace_bytes", "ls_sketch_indices", "ls_solve_ex",
               "ls_sketch_csr", "ls_sketch", "ls_factor", "ls_residual_gradient", "ls_correct",
               "ls_iterate", "ls_solve", "ls_default_opts"]:
         assert s in syms
@@ -50,3 +50,15 @@ def test_library_loads_and_binds(libpath):
     if st == ls.LS_OK:
         L.ls_destroy(h)
     assert L.ls_last_error(None) == b"null context"
+
+
+def test_damping_and_momentum_weights(libpath):
+    """App. B, Eqs. (B.2)-(B.3) with e = sqrt(n/d)."""
+    import paper_2311_04362_gb300 as ls
+    n, d = 50, 1000
+    e2 = n / d
+    o = ls.damping_opts(n, d)
+    assert o.alpha == pytest.approx((1 - e2) ** 2 / (1 + e2), rel=1e-15) and o.beta == 0.0
+    o = ls.momentum_opts(n, d)
+    assert o.alpha == pytest.approx((1 - e2) ** 2, rel=1e-15) and o.beta == pytest.approx(e2, rel=1e-15)
+    assert o.use_stop == 1 and o.rho == 0.04
