@@ -160,6 +160,24 @@ LS_API ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, 
                      const double* b, const double* R, int64_t ldr, double* x, int q,
                      const ls_opts* opts, ls_info* info);
 
+/* One problem of a batch (ls_solve_batched).  All pointers are device
+ * pointers: row-major A (m x n, lda even >= n, 16-byte aligned), b (m), x (n,
+ * output: the final iterate; left unwritten when the sketch is rank
+ * deficient).  d is the embedding dimension and seed keys the problem's
+ * sparse sign embedding (ls_sketch_indices with this seed).  Optional outputs
+ * (NULL to skip): B_out receives [S A, S b] before factorisation (d x (n+1),
+ * column-major, leading dimension d), R_out the triangular factor (n x n,
+ * column-major, leading dimension n, zero below the diagonal). */
+typedef struct {
+    const double* A;
+    const double* b;
+    double* x;
+    int64_t m, n, lda, d;
+    uint64_t seed;
+    double* B_out;
+    double* R_out;
+} ls_problem;
+
 /* App. B, Eqs. (B.2) and (B.3): set opts->alpha / opts->beta for iterative
  * sketching with damping (alpha = (1-e^2)^2/(1+e^2), beta = 0) or with
  * momentum (alpha = (1-e^2)^2, beta = e^2), with the paper's recommended
@@ -174,6 +192,18 @@ LS_API void ls_opts_momentum(ls_opts* opts, int64_t n, int64_t d);
 LS_API ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n,
                    int64_t lda, int64_t d, int zeta, int q, uint64_t seed, double* x,
                    ls_info* info);
+
+/* Solve `nprob` independent problems of different shapes together (each one
+ * exactly as ls_solve_ex would: sketch, Householder QR, sketch-and-solve
+ * start, refinement with the stopping rule), with one kernel launch per
+ * phase for the whole batch.  Each problem's sketch is bit-identical to
+ * ls_sketch of that problem.  probs: host array; infos: host array of nprob
+ * (may be NULL), per problem iterations / stop reason (0 rule held, 1 q
+ * reached, 2 stop rule off, 3 non-finite, 4 rank deficient) and estimates.
+ * Limits: n <= 1024 per problem, sum of m and sum of d below 2^31.
+ * Returns LS_OK when the batch ran (per-problem outcomes are in infos). */
+LS_API ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int nprob, int zeta, int q,
+                                  const ls_opts* opts, ls_info* infos);
 
 /* ls_solve with iteration options (stopping rule constants, extra updates,
  * damping / momentum of App. B); opts may be NULL for the defaults. */

@@ -42,6 +42,12 @@ class ls_opts(C.Structure):
                 ("alpha", C.c_double), ("beta", C.c_double)]
 
 
+class ls_problem(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("b", C.c_void_p), ("x", C.c_void_p), ("m", C.c_int64), ("n", C.c_int64),
+                ("lda", C.c_int64), ("d", C.c_int64), ("seed", C.c_uint64), ("B_out", C.c_void_p),
+                ("R_out", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -85,6 +91,8 @@ def lib():
     L.ls_solve_ex.restype = S
     L.ls_opts_damping.argtypes = [C.POINTER(ls_opts), I64, I64]
     L.ls_opts_momentum.argtypes = [C.POINTER(ls_opts), I64, I64]
+    L.ls_solve_batched.argtypes = [P, C.POINTER(ls_problem), I, I, I, C.POINTER(ls_opts), C.POINTER(ls_info)]
+    L.ls_solve_batched.restype = S
     L.ls_residual_gradient_noalloc.argtypes = [P, P, I64, I64, I64, P, P, P, P, P, P]
     L.ls_residual_gradient_noalloc.restype = S
     _lib = L
@@ -208,6 +216,21 @@ class Context:
         st = lib().ls_solve(self._h, _ptr(A), _ptr(b), m, n, lda, d, zeta, q, seed, _ptr(x), C.byref(info))
         self._check(st, allow=(LS_OK, LS_ENOTCONV))
         return st, info
+
+    def ls_solve_batched(self, probs, zeta, q, opts=None, infos=None):
+        """probs: sequence of ls_problem (or dicts with its fields; tensors are
+        taken by pointer).  Returns the ls_info array (one per problem)."""
+        arr = (ls_problem * len(probs))()
+        for i, p in enumerate(probs):
+            if isinstance(p, ls_problem):
+                arr[i] = p
+                continue
+            arr[i] = ls_problem(_ptr(p["A"]), _ptr(p["b"]), _ptr(p["x"]), p["m"], p["n"], p["lda"], p["d"],
+                                p.get("seed", i), _ptr(p.get("B_out")), _ptr(p.get("R_out")))
+        infos = infos if infos is not None else (ls_info * len(probs))()
+        self._check(lib().ls_solve_batched(self._h, arr, len(probs), zeta, q,
+                                           C.byref(opts) if opts is not None else None, infos))
+        return infos
 
 
 def solve(A, b, d=None, zeta=8, q=100, seed=0, ctx: Context | None = None):

@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <vector>
+
 #include "ls_internal.cuh"
 
 using namespace lsk;
@@ -575,6 +577,138 @@ ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
   st = iterate_impl(ctx, A, m, n, lda, b, R, ldr, x, q, opts, ne, ce, cc, info);
   info->launches = (int)(ctx->launches - l0);
   return st;
+}
+
+ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zeta, int q, const ls_opts* opts,
+                           ls_info* infos) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  if (np < 0 || (np > 0 && !probs)) return fail(ctx, LS_EINVAL, "invalid problem array");
+  if (np == 0) return LS_OK;
+  if (zeta < 1 || zeta > 32) return fail(ctx, LS_EINVAL, "zeta = %d must be in [1, 32]", zeta);
+  if (q <= 0) q = 100;
+  ls_opts o;
+  ls_default_opts(&o);
+  if (opts) o = *opts;
+  int64_t msum = 0, dsum = 0;
+  for (int p = 0; p < np; ++p) {
+    const ls_problem& pr = probs[p];
+    ls_status st;
+    if (!pr.b || !pr.x) return fail(ctx, LS_EINVAL, "problem %d: null b or x", p);
+    if ((st = check_A(ctx, pr.A, pr.m, pr.n, pr.lda))) {
+      const std::string why = ctx->err;
+      return fail(ctx, st, "problem %d: %s", p, why.c_str());
+    }
+    if (pr.d < pr.n || pr.d > INT32_MAX || zeta > pr.d)
+      return fail(ctx, LS_EINVAL, "problem %d: need n <= d, zeta <= d", p);
+    if (pr.n > 1024) return fail(ctx, LS_EINVAL, "problem %d: n = %lld above the batched limit 1024", p, (long long)pr.n);
+    msum += pr.m;
+    dsum += pr.d;
+  }
+  if (msum > INT32_MAX || dsum > INT32_MAX) return fail(ctx, LS_EINVAL, "sum of m or of d reaches 2^31");
+  cudaSetDevice(ctx->device);
+  std::vector<char> hP(bprob_bytes() * (size_t)np);
+  BProb* hp = reinterpret_cast<BProb*>(hP.data());
+  BatchPlan pl;
+  batch_plan(probs, np, hp, pl);
+  std::vector<int64_t> hoffs(3 * (size_t)np);
+  batch_offsets(hp, np, hoffs.data(), hoffs.data() + np, hoffs.data() + 2 * np);
+
+  auto carve_all = [&](Carve& c, BProb** dP, int64_t** doff3, SketchScratch* sk, BPools* pools, unsigned int** active) {
+    *dP = reinterpret_cast<BProb*>(c.take<char>(bprob_bytes() * (size_t)np));
+    *doff3 = c.take<int64_t>(3 * (size_t)np);
+    *sk = carve_sketch(c, pl.mtotal, pl.dtotal, zeta);
+    pools->B = c.take<double>((size_t)pl.btotal);
+    pools->R = c.take<double>((size_t)pl.rtotal);
+    pools->Rt = c.take<double>((size_t)pl.rtotal);
+    pools->inv_diag = c.take<double>((size_t)pl.vtotal);
+    pools->x_prev = c.take<double>((size_t)pl.vtotal);
+    pools->y = c.take<double>((size_t)pl.vtotal);
+    pools->dvec = c.take<double>((size_t)pl.vtotal);
+    pools->work = c.take<double>((size_t)pl.vtotal);
+    pools->v = c.take<double>((size_t)pl.vtotal);
+    pools->w = c.take<double>((size_t)pl.vtotal);
+    pools->xi = c.take<double>((size_t)pl.vtotal);
+    pools->slots = c.take<double>(64 * (size_t)np);
+    pools->est = c.take<double>(2 * (size_t)np);
+    pools->part = c.take<double>((size_t)pl.ptotal);
+    pools->r_prev = c.take<double>((size_t)pl.mtotal);
+    pools->st = c.take<IterState>((size_t)np);
+    pools->pstatus = c.take<unsigned int>((size_t)np);
+    *active = c.take<unsigned int>(4);
+  };
+  BProb* dP; int64_t* doff3; SketchScratch sk; BPools pools; unsigned int* active;
+  Carve probe(nullptr);
+  carve_all(probe, &dP, &doff3, &sk, &pools, &active);
+  ls_status st;
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  carve_all(cc, &dP, &doff3, &sk, &pools, &active);
+  if ((st = reset_status(ctx))) return st;
+  CUDA_TRY(ctx, cudaMemcpyAsync(dP, hp, bprob_bytes() * (size_t)np, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(doff3, hoffs.data(), sizeof(int64_t) * 3 * np, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(pools.pstatus, 0, sizeof(unsigned int) * np, ctx->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(pools.r_prev, 0, sizeof(double) * pl.mtotal, ctx->stream));
+  const long long l0 = ctx->launches;
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+  // sketch
+  CUDA_TRY(ctx, launch_b_sketch_indices(ctx, dP, doff3, pl, zeta, sk.rows, sk.signs));
+  if ((st = sketch_csr_impl(ctx, pl.mtotal, pl.dtotal, zeta, sk.rows, sk.signs, sk.row_ptr, sk.ent, sk.fill)))
+    return st;
+  CUDA_TRY(ctx, launch_b_gather(ctx, dP, doff3 + np, pl, sk.row_ptr, sk.ent, 1.0 / std::sqrt((double)zeta), pools.B));
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+  for (int p = 0; p < np; ++p)
+    if (probs[p].B_out)
+      CUDA_TRY(ctx, cudaMemcpyAsync(probs[p].B_out, pools.B + batch_boff(hp, p),
+                                    sizeof(double) * (size_t)probs[p].d * (probs[p].n + 1),
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
+  // factor
+  CUDA_TRY(ctx, launch_b_factor(ctx, dP, pl, pools));
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
+  for (int p = 0; p < np; ++p)
+    if (probs[p].R_out)
+      CUDA_TRY(ctx, cudaMemcpyAsync(probs[p].R_out, pools.R + batch_roff(hp, p),
+                                    sizeof(double) * (size_t)probs[p].n * probs[p].n, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+  // iterate
+  CUDA_TRY(ctx, launch_b_iter_init(ctx, dP, pl, pools, o.gamma, o.rho, o.alpha, o.beta));
+  unsigned int* hact = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(ctx->h_pinned) + 2048);
+  for (int i = 0; i < q; ++i) {
+    CUDA_TRY(ctx, launch_b_pass(ctx, dP, doff3 + 2 * np, pl, pools));
+    CUDA_TRY(ctx, cudaMemsetAsync(active, 0, sizeof(unsigned int), ctx->stream));
+    CUDA_TRY(ctx, launch_b_step(ctx, dP, pl, pools, o.use_stop, o.extra_iters, active));
+    if ((i & 7) == 7 && i + 1 < q) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(hact, active, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+      CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      if (*hact == 0) break;
+    }
+  }
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], ctx->stream));
+  std::vector<IterState> hst((size_t)np);
+  std::vector<double> hest(2 * (size_t)np);
+  CUDA_TRY(ctx, cudaMemcpyAsync(hst.data(), pools.st, sizeof(IterState) * np, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(hest.data(), pools.est, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, ctx->stream));
+  if ((st = sync_and_check(ctx))) return st;
+  if (infos) {
+    float ms[3] = {0, 0, 0};
+    cudaEventElapsedTime(&ms[0], ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&ms[1], ctx->ev[1], ctx->ev[2]);
+    cudaEventElapsedTime(&ms[2], ctx->ev[2], ctx->ev[3]);
+    for (int p = 0; p < np; ++p) {
+      ls_info& in = infos[p];
+      std::memset(&in, 0, sizeof in);
+      const IterState& s = hst[p];
+      in.iters = s.iter;
+      in.stop_reason = s.stop_reason == 4 ? 4 : (s.done ? (s.nonfinite ? 3 : 0) : (o.use_stop ? 1 : 2));
+      in.res_norm = s.rnorm;
+      in.step_norm = s.dnorm;
+      in.normest = hest[2 * p];
+      in.condest = hest[2 * p + 1];
+      in.ms_sketch = ms[0]; in.ms_factor = ms[1]; in.ms_iterate = ms[2];
+      in.launches = (int)(ctx->launches - l0);
+    }
+  }
+  return LS_OK;
 }
 
 ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n, int64_t lda, int64_t d,

@@ -253,4 +253,47 @@ __device__ inline double cl_norm1(const CL& cl, int n, const double* v, double* 
   return cl_sum(cl, cta_sum(s), slots);
 }
 
+// Power-method and 1-norm estimator helpers shared by the single-problem and
+// batched post-factor kernels.
+__device__ inline double sgn1(double v) { return v >= 0.0 ? 1.0 : -1.0; }
+
+__device__ inline double power_start(uint64_t seed, uint32_t domain, int i) {
+  WordStream s(seed, (uint64_t)i, domain);
+  const uint32_t w0 = s.next(), w1 = s.next();
+  const uint64_t bits = ((uint64_t)w0 << 21) | (uint64_t)(w1 >> 11);
+  return 2.0 * ((double)bits * 0x1.0p-53) - 1.0;
+}
+
+// w = R v (rows i of R, from Rt) for owned rows.
+__device__ inline void cl_matvec_R(const CL& cl, const double* Rt, int n, const double* v, double* w) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nb = (n + 31) / 32;
+  for (int b = cl.rank; b < nb; b += cl.ncta)
+    for (int i = 32 * b + warp; i < min(n, 32 * b + 32); i += nw) {
+      double s = 0.0;
+      for (int k = i + lane; k < n; k += 32) s += __ldg(Rt + (size_t)k + (size_t)i * n) * __ldcg(v + k);
+      s = warp_sum(s);
+      if (lane == 0) __stcg(w + i, s);
+    }
+}
+
+// v = R^T w (column i of R) for owned rows.
+__device__ inline void cl_matvec_RT(const CL& cl, const double* R, int64_t ldr, int n, const double* w, double* v) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nb = (n + 31) / 32;
+  for (int b = cl.rank; b < nb; b += cl.ncta)
+    for (int i = 32 * b + warp; i < min(n, 32 * b + 32); i += nw) {
+      double s = 0.0;
+      for (int k = lane; k <= i; k += 32) s += __ldg(R + (size_t)k + (size_t)i * ldr) * __ldcg(w + k);
+      s = warp_sum(s);
+      if (lane == 0) __stcg(v + i, s);
+    }
+}
+
+__device__ inline int power_steps(int n) {
+  int k = 0;
+  while (k < 64 && exp((double)k) < (double)n) ++k;
+  return k < 1 ? 1 : k;
+}
+
 }  // namespace lsk

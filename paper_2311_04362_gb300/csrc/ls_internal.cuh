@@ -319,6 +319,37 @@ struct StepArgs {
   double* y_out; double* d_out;
 };
 cudaError_t launch_iter_step(ls_ctx* ctx, const StepArgs& a);
+
+// batched path (batched.cu)
+struct BProb;
+struct BPools {
+  double* B; double* R; double* Rt; double* inv_diag;
+  double* x_prev; double* y; double* dvec; double* work; double* v; double* w; double* xi;
+  double* slots; double* est; double* part; double* r_prev;
+  IterState* st;
+  unsigned int* pstatus;
+};
+struct BatchPlan {
+  int np;
+  int64_t mtotal, dtotal, btotal, rtotal, vtotal, ttotal, ptotal;
+  int max_n, max_tile_doubles;
+};
+size_t bprob_bytes();
+void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl);
+void batch_offsets(const BProb* P, int np, int64_t* moffs, int64_t* doffs, int64_t* toffs);
+int64_t batch_boff(const BProb* P, int p);
+int64_t batch_roff(const BProb* P, int p);
+cudaError_t launch_b_sketch_indices(ls_ctx* ctx, const BProb* dP, const int64_t* dmoffs, const BatchPlan& pl,
+                                    int zeta, int32_t* rows, uint32_t* signs);
+cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* ddoffs, const BatchPlan& pl,
+                            const int64_t* row_ptr, const uint32_t* ent, double scale, double* Bpool);
+cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools);
+cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools,
+                               double gamma, double rho, double alpha, double beta);
+cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int64_t* dtoffs, const BatchPlan& pl,
+                          const BPools& pools);
+cudaError_t launch_b_step(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int use_stop,
+                          int extra, unsigned int* active);
 cudaError_t launch_correct(ls_ctx* ctx, const StepArgs& a);
 
 }  // namespace lsk
