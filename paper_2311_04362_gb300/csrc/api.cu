@@ -614,7 +614,8 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
   std::vector<int64_t> hoffs(3 * (size_t)np);
   batch_offsets(hp, np, hoffs.data(), hoffs.data() + np, hoffs.data() + 2 * np);
 
-  auto carve_all = [&](Carve& c, BProb** dP, int64_t** doff3, SketchScratch* sk, BPools* pools, unsigned int** active) {
+  auto carve_all = [&](Carve& c, BProb** dP, int64_t** doff3, SketchScratch* sk, BPools* pools, int** alist,
+                       int64_t** aoff, int64_t** cnt) {
     *dP = reinterpret_cast<BProb*>(c.take<char>(bprob_bytes() * (size_t)np));
     *doff3 = c.take<int64_t>(3 * (size_t)np);
     *sk = carve_sketch(c, pl.mtotal, pl.dtotal, zeta);
@@ -635,15 +636,17 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
     pools->r_prev = c.take<double>((size_t)pl.mtotal);
     pools->st = c.take<IterState>((size_t)np);
     pools->pstatus = c.take<unsigned int>((size_t)np);
-    *active = c.take<unsigned int>(4);
+    *alist = c.take<int>((size_t)np);
+    *aoff = c.take<int64_t>((size_t)np);
+    *cnt = c.take<int64_t>(2);
   };
-  BProb* dP; int64_t* doff3; SketchScratch sk; BPools pools; unsigned int* active;
+  BProb* dP; int64_t* doff3; SketchScratch sk; BPools pools; int* alist; int64_t* aoff; int64_t* cnt;
   Carve probe(nullptr);
-  carve_all(probe, &dP, &doff3, &sk, &pools, &active);
+  carve_all(probe, &dP, &doff3, &sk, &pools, &alist, &aoff, &cnt);
   ls_status st;
   if ((st = ensure_arena(ctx, probe.off))) return st;
   Carve cc(ctx->arena);
-  carve_all(cc, &dP, &doff3, &sk, &pools, &active);
+  carve_all(cc, &dP, &doff3, &sk, &pools, &alist, &aoff, &cnt);
   if ((st = reset_status(ctx))) return st;
   CUDA_TRY(ctx, cudaMemcpyAsync(dP, hp, bprob_bytes() * (size_t)np, cudaMemcpyHostToDevice, ctx->stream));
   CUDA_TRY(ctx, cudaMemcpyAsync(doff3, hoffs.data(), sizeof(int64_t) * 3 * np, cudaMemcpyHostToDevice, ctx->stream));
@@ -653,9 +656,22 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
   // sketch
   CUDA_TRY(ctx, launch_b_sketch_indices(ctx, dP, doff3, pl, zeta, sk.rows, sk.signs));
-  if ((st = sketch_csr_impl(ctx, pl.mtotal, pl.dtotal, zeta, sk.rows, sk.signs, sk.row_ptr, sk.ent, sk.fill)))
+  if (b_csr_fits(pl)) {
+    // buckets above 1024 entries are sorted in global scratch; expect them
+    // only when some problem's mean bucket exceeds ~600
+    uint32_t* scratch = nullptr;
+    if (pl.max_fill * zeta > 600.0) {
+      if ((st = ensure_aux(ctx, &ctx->aux, &ctx->aux_bytes, sizeof(uint32_t) * 2 * (size_t)pl.mtotal * zeta)))
+        return st;
+      scratch = reinterpret_cast<uint32_t*>(ctx->aux);
+    }
+    CUDA_TRY(ctx, launch_b_csr(ctx, dP, pl, zeta, sk.rows, sk.signs, sk.row_ptr, sk.ent, scratch));
+  } else if ((st = sketch_csr_impl(ctx, pl.mtotal, pl.dtotal, zeta, sk.rows, sk.signs, sk.row_ptr, sk.ent,
+                                   sk.fill))) {
     return st;
-  CUDA_TRY(ctx, launch_b_gather(ctx, dP, doff3 + np, pl, sk.row_ptr, sk.ent, 1.0 / std::sqrt((double)zeta), pools.B));
+  }
+  CUDA_TRY(ctx, launch_b_gather(ctx, dP, doff3 + 2 * np, pl, sk.row_ptr, sk.ent, 1.0 / std::sqrt((double)zeta),
+                                pools.B));
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
   for (int p = 0; p < np; ++p)
     if (probs[p].B_out)
@@ -672,15 +688,16 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
                                     ctx->stream));
   // iterate
   CUDA_TRY(ctx, launch_b_iter_init(ctx, dP, pl, pools, o.gamma, o.rho, o.alpha, o.beta));
-  unsigned int* hact = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(ctx->h_pinned) + 2048);
+  CUDA_TRY(ctx, launch_b_compact(ctx, dP, pl, pools, alist, aoff, cnt));
+  int64_t* hcnt = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(ctx->h_pinned) + 2048);
   for (int i = 0; i < q; ++i) {
-    CUDA_TRY(ctx, launch_b_pass(ctx, dP, doff3 + 2 * np, pl, pools));
-    CUDA_TRY(ctx, cudaMemsetAsync(active, 0, sizeof(unsigned int), ctx->stream));
-    CUDA_TRY(ctx, launch_b_step(ctx, dP, pl, pools, o.use_stop, o.extra_iters, active));
+    CUDA_TRY(ctx, launch_b_pass(ctx, dP, alist, aoff, cnt, pl, pools));
+    CUDA_TRY(ctx, launch_b_step(ctx, dP, pl, pools, o.use_stop, o.extra_iters));
+    CUDA_TRY(ctx, launch_b_compact(ctx, dP, pl, pools, alist, aoff, cnt));
     if ((i & 7) == 7 && i + 1 < q) {
-      CUDA_TRY(ctx, cudaMemcpyAsync(hact, active, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+      CUDA_TRY(ctx, cudaMemcpyAsync(hcnt, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
       CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-      if (*hact == 0) break;
+      if (*hcnt == 0) break;
     }
   }
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], ctx->stream));

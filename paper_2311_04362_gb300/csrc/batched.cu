@@ -3,19 +3,27 @@
 // one launch per phase for the whole batch.
 //
 //  * sketch: k_b_sparse_sign writes every column's zeta rows as global bucket
-//    ids (problem offset + row), so the single-problem counting sort
-//    (k_hist, k_scan, k_scatter, k_bucket_sort) runs unchanged over the
-//    concatenated buckets; k_b_gather (one warp per bucket) forms B_p column
-//    by column with the same left-to-right sums as the single-problem path,
-//    so every B_p is bit-identical to ls_sketch of that problem.
+//    ids (problem offset + row); k_b_csr (one CTA per problem) counts, scans
+//    and scatters the problem's entries with shared-memory atomics and sorts
+//    every bucket (a warp-wide bitonic sort in shared memory; the CTA sorts
+//    buckets above 1024 entries in global scratch), so the CSR is the unique
+//    stable one; k_b_gather forms B_p with 32, 16, 8 or 4 lanes per bucket
+//    (one column per lane, the narrowest width that holds n + 1 columns) with
+//    the same left-to-right sums as the single-problem path, so every B_p is
+//    bit-identical to ls_sketch of that problem.
 //  * factor: one CTA per problem (k_b_householder: unblocked LAPACK-convention
 //    Householder on B_p in L2), then k_prepare_R-like and post-factor work
 //    per problem on 1-CTA clusters with the cluster_la.cuh routines.
-//  * iterate: k_b_pass walks the (problem, row tile) items of all active
-//    problems in a persistent grid (tile staged in shared memory, row dots by
-//    warps, A^T r by column threads, one partial per item); k_b_step (one
-//    CTA per problem) sums a problem's partials in item order, applies the
-//    stopping rule and does the two substitutions and the update.
+//  * iterate: k_b_compact lists the active problems and the prefix of their
+//    row tiles; k_b_pass, persistent (two CTAs per SM), walks those tiles with
+//    a two-buffer cp.async.bulk pipeline (rows of A land in shared memory at
+//    a stride = 2 mod 4 doubles, so column-wise reads are at most 2-way bank
+//    conflicted).  Each tile is used twice: row dots A_j x by (row, column
+//    chunk) threads -- no shuffle trees, the FP64 pipe does one FMA per
+//    element -- then c += A^T r by (column, row group) threads.  One partial
+//    (c, ||r||^2, ||r - r_prev||^2) per tile; k_b_step (one CTA per problem)
+//    sums a problem's partials in tile order, applies the stopping rule and
+//    does the two substitutions and the update.
 #include <algorithm>
 
 #include "cluster_la.cuh"
@@ -31,10 +39,14 @@ struct BProb {
   int64_t boff;      // sum of d (n + 1) (B pool)
   int64_t roff;      // sum of n^2 (R, Rt pools)
   int64_t voff;      // sum of n (vector pools)
-  int64_t toff;      // sum of row tiles (pass items)
+  int64_t toff;      // sum of gather warps (k_b_gather)
   int64_t poff;      // sum of tiles (n + 2) (partials)
-  int tr;            // rows per tile
-  int tiles;
+  int tr;            // rows per pass tile
+  int tiles;         // pass tiles
+  int ss;            // shared-memory row stride of a tile (doubles, = 2 mod 4)
+  int S;             // column chunks per row in the row-dot phase (S * tr <= 256)
+  int rowcopy;       // 1: one bulk copy per row (lda != ss), 0: one per tile
+  int gw;            // gather lanes per bucket (32, 16, 8 or 4)
 };
 
 size_t bprob_bytes() { return sizeof(BProb); }
@@ -84,40 +96,170 @@ __global__ void __launch_bounds__(256) k_b_sparse_sign(const BProb* __restrict__
   signs[g] = mask;
 }
 
-// One warp per global bucket: B_p[t, c] = s * (left-to-right sum of +-A_p[j, c]).
-__global__ void __launch_bounds__(256) k_b_gather(const BProb* __restrict__ P, const int64_t* __restrict__ doffs,
-                                                  int np, int64_t dtotal, const int64_t* __restrict__ row_ptr,
+// Largest bucket count handled by k_b_csr (shared-memory counters).
+static constexpr int kCsrMaxD = 12288;
+static constexpr int kCsrThreads = 512;
+static constexpr int kCsrWarpKeys = 1024;   // per-warp sort scratch (keys)
+
+// Warp-wide bitonic sort of s[0..P) ascending (P a power of two <= 1024).
+__device__ inline void warp_bitonic(uint32_t* s, int P, int lane) {
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < P; i += 32) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint32_t a = s[i], b = s[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) { s[i] = b; s[ixj] = a; }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// One CTA per problem: CSR of the problem's part of S (row_ptr over its d
+// buckets, entries (global column << 1 | negative) sorted within each bucket).
+// The entries of problem p occupy [moff * zeta, (moff + m) * zeta).
+__global__ void __launch_bounds__(kCsrThreads) k_b_csr(const BProb* __restrict__ P, int zeta,
+                                                       const int32_t* __restrict__ rows,
+                                                       const uint32_t* __restrict__ signs,
+                                                       int64_t* __restrict__ row_ptr, uint32_t* __restrict__ ent,
+                                                       uint32_t* __restrict__ scratch,
+                                                       unsigned int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char csr_smem[];
+  int* cnt = reinterpret_cast<int*>(csr_smem);                               // kCsrMaxD
+  uint32_t* wscr = reinterpret_cast<uint32_t*>(cnt + kCsrMaxD);              // 16 x 1024
+  __shared__ int wtot[32];
+  __shared__ int s_big;
+  const BProb pr = P[blockIdx.x];
+  const int d = (int)pr.d;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t e0 = pr.moff * zeta;                 // first entry of this problem
+  const int64_t ne = pr.m * zeta;
+  const int32_t* rw = rows + e0;
+  for (int t = tid; t < d; t += kCsrThreads) cnt[t] = 0;
+  if (tid == 0) s_big = 0;
+  __syncthreads();
+  for (int64_t e = tid; e < ne; e += kCsrThreads) atomicAdd(&cnt[rw[e] - (int)pr.doff], 1);
+  __syncthreads();
+  // exclusive scan of cnt[0..d) in chunks of the block
+  int carry = 0;
+  for (int base = 0; base < d; base += kCsrThreads) {
+    const int t = base + tid;
+    const int v = (t < d) ? cnt[t] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int w = (lane < kCsrThreads / 32) ? wtot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wtot[lane] = w;
+    }
+    __syncthreads();
+    const int excl = carry + (warp ? wtot[warp - 1] : 0) + incl - v;
+    if (t < d) {
+      cnt[t] = excl;
+      row_ptr[pr.doff + t] = e0 + excl;
+      if (v > kCsrWarpKeys) s_big = 1;
+    }
+    carry += wtot[kCsrThreads / 32 - 1];
+    __syncthreads();
+  }
+  if (tid == 0) row_ptr[pr.doff + d] = e0 + ne;      // equals the next problem's first row_ptr
+  // scatter (bucket order of equal keys is fixed by the sort below)
+  for (int64_t e = tid; e < ne; e += kCsrThreads) {
+    const int64_t j = e / zeta;
+    const int k = (int)(e - j * zeta);
+    const uint32_t neg = (signs[pr.moff + j] >> k) & 1u;
+    const int pos = atomicAdd(&cnt[rw[e] - (int)pr.doff], 1);
+    ent[e0 + pos] = ((uint32_t)(pr.moff + j) << 1) | neg;
+  }
+  __syncthreads();
+  // cnt[t] is now the end of bucket t (= start of bucket t + 1)
+  uint32_t* mys = wscr + warp * kCsrWarpKeys;
+  for (int t = warp; t < d; t += kCsrThreads / 32) {
+    const int b0 = t ? cnt[t - 1] : 0, sz = cnt[t] - b0;
+    if (sz <= 1 || sz > kCsrWarpKeys) continue;
+    int Pw = 1;
+    while (Pw < sz) Pw <<= 1;
+    for (int i = lane; i < Pw; i += 32) mys[i] = (i < sz) ? ent[e0 + b0 + i] : 0xFFFFFFFFu;
+    __syncwarp();
+    warp_bitonic(mys, Pw, lane);
+    for (int i = lane; i < sz; i += 32) ent[e0 + b0 + i] = mys[i];
+    __syncwarp();
+  }
+  if (!s_big) return;                                  // uniform
+  if (!scratch) {
+    if (tid == 0) atomicOr(status, LS_DEV_BADSIZE);
+    return;
+  }
+  for (int t = 0; t < d; ++t) {                        // rare: buckets above 1024 entries
+    const int b0 = t ? cnt[t - 1] : 0, sz = cnt[t] - b0;
+    if (sz <= kCsrWarpKeys) continue;
+    int Pb = 1;
+    while (Pb < sz) Pb <<= 1;
+    uint32_t* buf = scratch + 2 * (e0 + b0);
+    for (int i = tid; i < Pb; i += kCsrThreads) buf[i] = (i < sz) ? ent[e0 + b0 + i] : 0xFFFFFFFFu;
+    __syncthreads();
+    bitonic(buf, Pb);
+    for (int i = tid; i < sz; i += kCsrThreads) ent[e0 + b0 + i] = buf[i];
+    __syncthreads();
+  }
+}
+
+// B_p[t, c] = s * (left-to-right sum over the bucket of +-[A_p b_p][j, c]).
+// A warp serves 32 / gw buckets of one problem, gw lanes each (one column per
+// lane, column chunks of gw).  Warps are numbered per problem from woffs.
+__global__ void __launch_bounds__(256) k_b_gather(const BProb* __restrict__ P, const int64_t* __restrict__ woffs,
+                                                  int np, int64_t nwarps, const int64_t* __restrict__ row_ptr,
                                                   const uint32_t* __restrict__ ent, double scale,
                                                   double* __restrict__ Bpool) {
-  const int64_t tg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t wg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (tg >= dtotal) return;
-  const int p = find_problem(doffs, np, tg);
+  if (wg >= nwarps) return;
+  const int p = find_problem(woffs, np, wg);
   const BProb pr = P[p];
-  const int64_t t = tg - pr.doff;
+  const int gw = pr.gw;
+  const int64_t t = (wg - pr.toff) * (32 / gw) + lane / gw;   // bucket within the problem
+  if (t >= pr.d) return;
+  const int cl = lane % gw;
+  const int64_t tg = pr.doff + t;
   const int64_t e0 = row_ptr[tg], e1 = row_ptr[tg + 1];
   double* B = Bpool + pr.boff;
-  for (int64_t c0 = 0; c0 <= pr.n; c0 += 64) {
-    const int64_t c = c0 + 2 * lane;
-    // this lane's columns: c, c+1 of [A b] (c == n is b)
-    const bool has0 = c <= pr.n, has1 = c + 1 <= pr.n;
-    double a0 = 0.0, a1 = 0.0;
-    for (int64_t e = e0; e < e1; ++e) {
-      const uint32_t en = __ldg(ent + e);
-      const int64_t j = (int64_t)(en >> 1) - pr.moff;
-      double v0 = 0.0, v1 = 0.0;
-      if (c + 1 < pr.n) {
-        const double2 v = __ldg(reinterpret_cast<const double2*>(pr.A + j * pr.lda + c));
-        v0 = v.x; v1 = v.y;
-      } else {
-        if (has0) v0 = (c < pr.n) ? __ldg(pr.A + j * pr.lda + c) : __ldg(pr.b + j);
-        if (has1) v1 = (c + 1 < pr.n) ? __ldg(pr.A + j * pr.lda + c + 1) : __ldg(pr.b + j);
-      }
-      if (en & 1u) { a0 = a0 - v0; a1 = a1 - v1; }
-      else { a0 = a0 + v0; a1 = a1 + v1; }
+  const uint32_t mo = (uint32_t)pr.moff;              // entries hold global column ids
+  for (int64_t c = cl; c <= pr.n; c += gw) {
+    const bool isb = (c == pr.n);
+    const double* base = isb ? pr.b : (pr.A + c);
+    const int64_t stride = isb ? 1 : pr.lda;
+    double acc = 0.0;
+    int64_t e = e0;
+    for (; e + 4 <= e1; e += 4) {
+      const uint32_t n0 = __ldg(ent + e), n1 = __ldg(ent + e + 1), n2 = __ldg(ent + e + 2), n3 = __ldg(ent + e + 3);
+      const double v0 = __ldg(base + (int64_t)((n0 >> 1) - mo) * stride);
+      const double v1 = __ldg(base + (int64_t)((n1 >> 1) - mo) * stride);
+      const double v2 = __ldg(base + (int64_t)((n2 >> 1) - mo) * stride);
+      const double v3 = __ldg(base + (int64_t)((n3 >> 1) - mo) * stride);
+      acc = (n0 & 1u) ? acc - v0 : acc + v0;
+      acc = (n1 & 1u) ? acc - v1 : acc + v1;
+      acc = (n2 & 1u) ? acc - v2 : acc + v2;
+      acc = (n3 & 1u) ? acc - v3 : acc + v3;
     }
-    if (has0) B[t + c * pr.d] = scale * a0;
-    if (has1) B[t + (c + 1) * pr.d] = scale * a1;
+    for (; e < e1; ++e) {
+      const uint32_t n0 = __ldg(ent + e);
+      const double v0 = __ldg(base + (int64_t)((n0 >> 1) - mo) * stride);
+      acc = (n0 & 1u) ? acc - v0 : acc + v0;
+    }
+    B[t + c * pr.d] = scale * acc;
   }
 }
 
@@ -316,87 +458,218 @@ __global__ void k_b_iter_init(const BProb* __restrict__ P, int np, BPools pl, do
 }
 
 static constexpr int kBThreads = 256;
+static constexpr int kBTileCap = 6144;      // doubles per tile buffer (48 KB)
 
-// Persistent pass over all (problem, tile) items of active problems.
-__global__ void __launch_bounds__(kBThreads) k_b_pass(const BProb* __restrict__ P, const int64_t* __restrict__ toffs,
-                                                      int np, int64_t items, BPools pl) {
-  extern __shared__ double sb[];
-  __shared__ double rt[256];
-  __shared__ double red[2 * 8];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-    const int p = find_problem(toffs, np, it);
-    if (pl.st[p].done) continue;                       // uniform in the CTA
-    const BProb pr = P[p];
-    const int n = (int)pr.n, tr = pr.tr;
-    const int tile = (int)(it - pr.toff);
-    const int64_t row0 = (int64_t)tile * tr;
-    const int rows = (int)min((int64_t)tr, pr.m - row0);
-    double* xs = sb;                                   // n
-    double* ts = sb + ((n + 1) & ~1);                  // rows x n
-    for (int i = threadIdx.x; i < n; i += kBThreads) xs[i] = pr.x[i];
-    for (int e = threadIdx.x; e < rows * n; e += kBThreads) {
-      const int r = e / n, c = e - r * n;
-      ts[e] = __ldg(pr.A + (row0 + r) * pr.lda + c);
+// Active problems in index order (alist) and the exclusive prefix of their
+// pass tiles (aoff); cnt[0] = active problems, cnt[1] = their tiles.
+__global__ void __launch_bounds__(1024) k_b_compact(const BProb* __restrict__ P, int np,
+                                                    const IterState* __restrict__ st, int* __restrict__ alist,
+                                                    int64_t* __restrict__ aoff, int64_t* __restrict__ cnt) {
+  __shared__ int64_t wa[32], wt[32];
+  __shared__ int64_t carry_a, carry_t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) { carry_a = 0; carry_t = 0; }
+  __syncthreads();
+  for (int base = 0; base < np; base += blockDim.x) {
+    const int p = base + threadIdx.x;
+    const int64_t fa = (p < np && !st[p].done) ? 1 : 0;
+    const int64_t ft = fa ? (int64_t)P[p].tiles : 0;
+    int64_t ia = fa, it = ft;                         // inclusive warp scans
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t ya = __shfl_up_sync(0xffffffffu, ia, o), yt = __shfl_up_sync(0xffffffffu, it, o);
+      if (lane >= o) { ia += ya; it += yt; }
+    }
+    if (lane == 31) { wa[warp] = ia; wt[warp] = it; }
+    __syncthreads();
+    if (warp == 0) {
+      int64_t xa = (lane < (int)(blockDim.x >> 5)) ? wa[lane] : 0, xt = (lane < (int)(blockDim.x >> 5)) ? wt[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t ya = __shfl_up_sync(0xffffffffu, xa, o), yt = __shfl_up_sync(0xffffffffu, xt, o);
+        if (lane >= o) { xa += ya; xt += yt; }
+      }
+      wa[lane] = xa; wt[lane] = xt;                   // inclusive over warps
     }
     __syncthreads();
-    // phase 1: r_j = b_j - A_j x (warp per row)
-    double rn2 = 0.0, dn2 = 0.0;
-    for (int r = warp; r < rows; r += kBThreads / 32) {
-      double dot = 0.0;
-      for (int c = lane; c < n; c += 32) dot += ts[r * n + c] * xs[c];
-      dot = warp_sum(dot);
-      if (lane == 0) {
-        const int64_t j = row0 + r;
-        const double rj = __ldg(pr.b + j) - dot;
-        double* rp = pl.r_prev + pr.moff + j;
-        const double dl = rj - *rp;
-        *rp = rj;
-        rn2 += rj * rj;
-        dn2 += dl * dl;
-        rt[r] = rj;
+    const int64_t pa = carry_a + (warp ? wa[warp - 1] : 0) + ia - fa;   // exclusive
+    const int64_t pt = carry_t + (warp ? wt[warp - 1] : 0) + it - ft;
+    if (fa) { alist[pa] = p; aoff[pa] = pt; }
+    __syncthreads();
+    if (threadIdx.x == 0) { carry_a += wa[(blockDim.x >> 5) - 1]; carry_t += wt[(blockDim.x >> 5) - 1]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { cnt[0] = carry_a; cnt[1] = carry_t; }
+}
+
+__device__ inline void bulk_load(void* smem_dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(smem_dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+struct BItem {
+  int64_t v;        // tile index in the active list (-1: none)
+  int p, tile;
+};
+
+// Issue the copies of one tile of problem pr into buf (warp 0; lane 0 sets
+// the expected bytes first).
+__device__ inline void b_issue_tile(const BProb& pr, int tile, double* buf, uint64_t* bar, int lane) {
+  const int64_t row0 = (int64_t)tile * pr.tr;
+  const int rows = (int)min((int64_t)pr.tr, pr.m - row0);
+  const uint32_t row_bytes = (uint32_t)(pr.lda * sizeof(double));
+  if (lane == 0) mbar_arrive_expect_tx(bar, row_bytes * (uint32_t)rows);
+  __syncwarp();
+  const double* src = pr.A + row0 * pr.lda;
+  if (pr.rowcopy) {
+    for (int r = lane; r < rows; r += 32) bulk_load(buf + (size_t)r * pr.ss, src + (size_t)r * pr.lda, row_bytes, bar);
+  } else if (lane == 0) {
+    bulk_load(buf, src, row_bytes * (uint32_t)rows, bar);
+  }
+}
+
+__device__ inline BItem b_locate(const int* __restrict__ alist, const int64_t* __restrict__ aoff, int na,
+                                 const BProb* __restrict__ P, int64_t v, int64_t items) {
+  BItem it{-1, 0, 0};
+  if (v >= items) return it;
+  const int i = find_problem(aoff, na, v);
+  it.v = v;
+  it.p = alist[i];
+  it.tile = (int)(v - aoff[i]);
+  return it;
+}
+
+// Persistent pass over the tiles of the active problems.
+__global__ void __launch_bounds__(kBThreads, 2) k_b_pass(const BProb* __restrict__ P, const int* __restrict__ alist,
+                                                         const int64_t* __restrict__ aoff,
+                                                         const int64_t* __restrict__ cnt, BPools pl, int max_n,
+                                                         unsigned int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* buf0 = reinterpret_cast<double*>(smem_raw);
+  double* xs = buf0 + 2 * kBTileCap;                 // max_n (even)
+  double* part1 = xs + ((max_n + 1) & ~1);           // 256
+  double* rt = part1 + kBThreads;                    // 256
+  double* q1 = rt + kBThreads;                       // 256: r_j^2
+  double* q2 = q1 + kBThreads;                       // 256: (r_j - r_prev_j)^2
+  double* gs = q2 + kBThreads;                       // 256: phase-2 group sums
+  uint64_t* bar = reinterpret_cast<uint64_t*>(gs + kBThreads);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int na = (int)cnt[0];
+  const int64_t items = cnt[1];
+  if ((int64_t)blockIdx.x >= items) return;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  BItem cur = b_locate(alist, aoff, na, P, blockIdx.x, items);
+  if (warp == 0) b_issue_tile(P[cur.p], cur.tile, buf0, &bar[0], lane);
+  int k = 0;
+  while (cur.v >= 0) {
+    const BItem nxt = b_locate(alist, aoff, na, P, cur.v + gridDim.x, items);
+    double* tl = buf0 + (size_t)(k & 1) * kBTileCap;
+    // the other buffer was last read by the previous tile, finished at the
+    // closing __syncthreads
+    if (warp == 0 && nxt.v >= 0)
+      b_issue_tile(P[nxt.p], nxt.tile, buf0 + (size_t)((k + 1) & 1) * kBTileCap, &bar[(k + 1) & 1], lane);
+    const BProb pr = P[cur.p];
+    const int n = (int)pr.n, TR = pr.tr, ss = pr.ss, S = pr.S;
+    const int64_t row0 = (int64_t)cur.tile * TR;
+    const int rows = (int)min((int64_t)TR, pr.m - row0);
+    for (int i = tid; i < n; i += kBThreads) xs[i] = pr.x[i];
+    const bool ok = mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1, gtimer() + LS_WAIT_NS);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(status, LS_DEV_TIMEOUT);
+      if (tid == 0 && nxt.v >= 0) mbar_wait_bounded(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1, gtimer() + LS_WAIT_NS);
+      return;
+    }
+    // phase 1: partial row dots, thread = (row r, column chunk s)
+    const int clen = (n + S - 1) / S;
+    if (tid < S * TR) {
+      const int r = tid % TR, sidx = tid / TR;
+      if (r < rows) {
+        const int c0 = sidx * clen, c1 = min(n, c0 + clen);
+        const double* a = tl + (size_t)r * ss;
+        // four interleaved accumulators: a dot of rounding error ~ (len/4 + 2) u
+        // instead of len u (the stopping rule compares r_i - r_{i-1} with u)
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+        int c = c0;
+        for (; c + 3 < c1; c += 4) {
+          d0 = fma(a[c], xs[c], d0);
+          d1 = fma(a[c + 1], xs[c + 1], d1);
+          d2 = fma(a[c + 2], xs[c + 2], d2);
+          d3 = fma(a[c + 3], xs[c + 3], d3);
+        }
+        if (c < c1) d0 = fma(a[c], xs[c], d0);
+        if (c + 1 < c1) d1 = fma(a[c + 1], xs[c + 1], d1);
+        if (c + 2 < c1) d2 = fma(a[c + 2], xs[c + 2], d2);
+        part1[tid] = (d0 + d1) + (d2 + d3);
       }
     }
-    if (lane == 0) { red[warp] = rn2; red[8 + warp] = dn2; }
     __syncthreads();
-    // phase 2: c_k = sum_r A_rk r_r over the tile (column threads, row groups)
-    double* out = pl.part + pr.poff + (int64_t)tile * (n + 2);
+    double* rp = pl.r_prev + pr.moff + row0;
+    if (tid < TR) {
+      double v1 = 0.0, v2 = 0.0;
+      if (tid < rows) {
+        double dot = 0.0;
+        for (int sidx = 0; sidx < S; ++sidx) dot += part1[sidx * TR + tid];
+        const double rj = __ldg(pr.b + row0 + tid) - dot;
+        const double dl = rj - rp[tid];
+        rp[tid] = rj;
+        rt[tid] = rj;
+        v1 = rj * rj;
+        v2 = dl * dl;
+      }
+      q1[tid] = v1;
+      q2[tid] = v2;
+    }
+    __syncthreads();
+    // phase 2: c_k = sum_r A_rk r_r over the tile
+    double* out = pl.part + pr.poff + (int64_t)cur.tile * (n + 2);
     if (n >= kBThreads) {
-      for (int c = threadIdx.x; c < n; c += kBThreads) {
-        double s = 0.0;
-        for (int r = 0; r < rows; ++r) s += ts[r * n + c] * rt[r];
-        out[c] = s;
+      for (int c = tid; c < n; c += kBThreads) {
+        double acc = 0.0;
+        for (int r = 0; r < rows; ++r) acc = fma(tl[(size_t)r * ss + c], rt[r], acc);
+        out[c] = acc;
       }
     } else {
       const int G = kBThreads / n;
-      const int g = threadIdx.x / n, c = threadIdx.x - g * n;
-      double s = 0.0;
-      if (g < G)
-        for (int r = g; r < rows; r += G) s += ts[r * n + c] * rt[r];
-      __syncthreads();
-      double* gs = ts;                                  // tile no longer needed
-      if (g < G) gs[g * n + c] = s;
-      __syncthreads();
-      for (int cc = threadIdx.x; cc < n; cc += kBThreads) {
-        double t = 0.0;
-        for (int q = 0; q < G; ++q) t += gs[q * n + cc];
-        out[cc] = t;
+      const int g = tid / n, c = tid - g * n;
+      if (g < G) {
+        double acc = 0.0;
+        for (int r = g; r < rows; r += G) acc = fma(tl[(size_t)r * ss + c], rt[r], acc);
+        gs[g * n + c] = acc;
       }
     }
-    if (threadIdx.x == 0) {
-      double s1 = 0.0, s2 = 0.0;
-      for (int w = 0; w < kBThreads / 32; ++w) { s1 += red[w]; s2 += red[8 + w]; }
-      out[n] = s1;
-      out[n + 1] = s2;
+    // the two squared norms of this tile (warps 0 and 1, fixed order)
+    if (warp < 2) {
+      const double* q = warp ? q2 : q1;
+      double v = 0.0;
+      for (int r = lane; r < TR; r += 32) v += q[r];
+      v = warp_sum(v);
+      if (lane == 0) out[n + warp] = v;
+    }
+    if (n < kBThreads) {
+      __syncthreads();
+      const int G = kBThreads / n;
+      for (int c = tid; c < n; c += kBThreads) {
+        double t = 0.0;
+        for (int g = 0; g < G; ++g) t += gs[g * n + c];
+        out[c] = t;
+      }
     }
     __syncthreads();
+    cur = nxt;
+    ++k;
   }
 }
 
 // One 1-CTA cluster per problem: sum partials (item order), stopping rule,
 // two substitutions, update.
-__global__ void __launch_bounds__(256) k_b_step(const BProb* __restrict__ P, BPools pl, int use_stop, int extra,
-                                                unsigned int* __restrict__ active) {
+__global__ void __launch_bounds__(256) k_b_step(const BProb* __restrict__ P, BPools pl, int use_stop, int extra) {
   const int p = blockIdx.x;
   IterState S = pl.st[p];
   if (S.done) return;
@@ -467,21 +740,28 @@ __global__ void __launch_bounds__(256) k_b_step(const BProb* __restrict__ P, BPo
     st.rnorm = rnorm;
     st.dnorm = dnorm;
     if (bad != 0.0) { st.nonfinite = 1; st.done = 1; st.stop_reason = 3; }
-    if (!st.done) atomicAdd(active, 1u);
   }
 }
 
 // ---------------------------------------------------------------- host side
 
-static int tile_rows(int64_t n) {
-  int64_t tr = 8192 / std::max<int64_t>(n, 1);
-  tr = std::max<int64_t>(8, std::min<int64_t>(256, tr));
-  return (int)tr;
+// Pass tile of a problem: shared-memory row stride ss = 2 mod 4 doubles (at
+// most 2-way bank conflicts when threads read down a column), rows per tile
+// tr = min(256, cap / ss), and S = 256 / tr column chunks per row dot.
+static void pass_tile(int64_t n, int64_t lda, BProb& b) {
+  const int ss = (int)((lda % 4 == 2) ? lda : lda + 2);
+  b.ss = ss;
+  b.rowcopy = (ss != lda) ? 1 : 0;
+  b.tr = std::max(1, std::min(256, kBTileCap / ss));
+  b.S = std::max(1, 256 / b.tr);
+  (void)n;
 }
 
 void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl) {
   pl.np = np;
-  pl.mtotal = pl.dtotal = pl.btotal = pl.rtotal = pl.vtotal = pl.ttotal = pl.ptotal = 0;
+  pl.mtotal = pl.dtotal = pl.btotal = pl.rtotal = pl.vtotal = pl.ttotal = pl.ptotal = pl.wtotal = 0;
+  pl.max_d = 0;
+  pl.max_fill = 0.0;
   pl.max_n = 0;
   pl.max_tile_doubles = 0;
   for (int p = 0; p < np; ++p) {
@@ -489,13 +769,17 @@ void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl) {
     BProb b{};
     b.A = q.A; b.b = q.b; b.x = q.x; b.m = q.m; b.n = q.n; b.lda = q.lda; b.d = q.d; b.seed = q.seed;
     b.moff = pl.mtotal; b.doff = pl.dtotal; b.boff = pl.btotal; b.roff = pl.rtotal; b.voff = pl.vtotal;
-    b.toff = pl.ttotal; b.poff = pl.ptotal;
-    b.tr = tile_rows(q.n);
+    b.toff = pl.wtotal; b.poff = pl.ptotal;
+    pass_tile(q.n, q.lda, b);
+    b.gw = (q.n + 1 > 16) ? 32 : (q.n + 1 > 8) ? 16 : (q.n + 1 > 4) ? 8 : 4;
     b.tiles = (int)((q.m + b.tr - 1) / b.tr);
     pl.mtotal += q.m; pl.dtotal += q.d; pl.btotal += q.d * (q.n + 1); pl.rtotal += q.n * q.n;
     pl.vtotal += q.n; pl.ttotal += b.tiles; pl.ptotal += (int64_t)b.tiles * (q.n + 2);
+    pl.wtotal += (q.d + (32 / b.gw) - 1) / (32 / b.gw);
+    pl.max_d = std::max<int64_t>(pl.max_d, q.d);
+    pl.max_fill = std::max<double>(pl.max_fill, (double)q.m / (double)q.d);
     pl.max_n = std::max<int>(pl.max_n, (int)q.n);
-    pl.max_tile_doubles = std::max<int>(pl.max_tile_doubles, (int)(((q.n + 1) & ~1LL) + (int64_t)b.tr * q.n));
+
     out[p] = b;
   }
 }
@@ -525,10 +809,23 @@ cudaError_t launch_b_sketch_indices(ls_ctx* ctx, const BProb* dP, const int64_t*
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* ddoffs, const BatchPlan& pl,
+cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* dwoffs, const BatchPlan& pl,
                             const int64_t* row_ptr, const uint32_t* ent, double scale, double* Bpool) {
-  k_b_gather<<<(unsigned)((pl.dtotal + 7) / 8), 256, 0, ctx->stream>>>(dP, ddoffs, pl.np, pl.dtotal, row_ptr, ent,
+  k_b_gather<<<(unsigned)((pl.wtotal + 7) / 8), 256, 0, ctx->stream>>>(dP, dwoffs, pl.np, pl.wtotal, row_ptr, ent,
                                                                        scale, Bpool);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+bool b_csr_fits(const BatchPlan& pl) { return pl.max_d <= kCsrMaxD; }
+
+cudaError_t launch_b_csr(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, int zeta, const int32_t* rows,
+                         const uint32_t* signs, int64_t* row_ptr, uint32_t* ent, uint32_t* scratch) {
+  const size_t smem = sizeof(int) * kCsrMaxD + sizeof(uint32_t) * (kCsrThreads / 32) * kCsrWarpKeys;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_b_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  k_b_csr<<<pl.np, kCsrThreads, smem, ctx->stream>>>(dP, zeta, rows, signs, row_ptr, ent, scratch, ctx->d_status);
   ++ctx->launches;
   return cudaGetLastError();
 }
@@ -555,28 +852,37 @@ cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int64_t* dtoffs, const BatchPlan& pl,
-                          const BPools& pools) {
-  const size_t smem = (size_t)pl.max_tile_doubles * sizeof(double);
+cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int* alist,
+                             int64_t* aoff, int64_t* cnt) {
+  k_b_compact<<<1, 1024, 0, ctx->stream>>>(dP, pl.np, pools.st, alist, aoff, cnt);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+size_t b_pass_smem(int max_n) {
+  return sizeof(double) * (2 * (size_t)kBTileCap + (size_t)((max_n + 1) & ~1) + 5 * kBThreads) + 2 * sizeof(uint64_t);
+}
+
+cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* aoff, const int64_t* cnt,
+                          const BatchPlan& pl, const BPools& pools) {
+  const size_t smem = b_pass_smem(pl.max_n);
   cudaError_t e;
-  if (smem > 48 * 1024) {
-    if ((e = cudaFuncSetAttribute(k_b_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return e;
-  }
+  if ((e = cudaFuncSetAttribute(k_b_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_pass, kBThreads, smem);
   const int64_t grid = std::min<int64_t>(pl.ttotal, (int64_t)ctx->num_sms * std::max(1, per_sm));
-  k_b_pass<<<(unsigned)grid, kBThreads, smem, ctx->stream>>>(dP, dtoffs, pl.np, pl.ttotal, pools);
+  k_b_pass<<<(unsigned)grid, kBThreads, smem, ctx->stream>>>(dP, alist, aoff, cnt, pools, pl.max_n, ctx->d_status);
   ++ctx->launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_step(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int use_stop,
-                          int extra, unsigned int* active) {
+                          int extra) {
   BPools pp = pools;
   const BProb* dPP = dP;
   int us = use_stop, ex = extra;
-  void* args[] = {(void*)&dPP, &pp, &us, &ex, &active};
+  void* args[] = {(void*)&dPP, &pp, &us, &ex};
   return launch_cluster_grid(ctx, (const void*)k_b_step, args, pl.np);
 }
 

@@ -206,6 +206,24 @@ __device__ inline bool grid_sync(const GridBar& gb, unsigned int nblocks) {
 }
 
 // ------------------------------------------------------------ reductions
+// Block-wide bitonic sort of s[0..P) ascending (P a power of two; every
+// thread of the block calls it).
+__device__ inline void bitonic(uint32_t* s, int P) {
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint32_t a = s[i], b = s[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) { s[i] = b; s[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 __device__ inline double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -332,8 +350,14 @@ struct BPools {
 struct BatchPlan {
   int np;
   int64_t mtotal, dtotal, btotal, rtotal, vtotal, ttotal, ptotal;
-  int max_n, max_tile_doubles;
+  int64_t wtotal;                // gather warps
+  int max_n, max_tile_doubles;   // max_tile_doubles: unused
+  int64_t max_d;
+  double max_fill;               // largest m / d (mean bucket size / zeta)
 };
+bool b_csr_fits(const BatchPlan& pl);
+cudaError_t launch_b_csr(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, int zeta, const int32_t* rows,
+                         const uint32_t* signs, int64_t* row_ptr, uint32_t* ent, uint32_t* scratch);
 size_t bprob_bytes();
 void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl);
 void batch_offsets(const BProb* P, int np, int64_t* moffs, int64_t* doffs, int64_t* toffs);
@@ -341,15 +365,17 @@ int64_t batch_boff(const BProb* P, int p);
 int64_t batch_roff(const BProb* P, int p);
 cudaError_t launch_b_sketch_indices(ls_ctx* ctx, const BProb* dP, const int64_t* dmoffs, const BatchPlan& pl,
                                     int zeta, int32_t* rows, uint32_t* signs);
-cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* ddoffs, const BatchPlan& pl,
+cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* dwoffs, const BatchPlan& pl,
                             const int64_t* row_ptr, const uint32_t* ent, double scale, double* Bpool);
 cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools);
 cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools,
                                double gamma, double rho, double alpha, double beta);
-cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int64_t* dtoffs, const BatchPlan& pl,
-                          const BPools& pools);
+cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int* alist,
+                             int64_t* aoff, int64_t* cnt);
+cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* aoff, const int64_t* cnt,
+                          const BatchPlan& pl, const BPools& pools);
 cudaError_t launch_b_step(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int use_stop,
-                          int extra, unsigned int* active);
+                          int extra);
 cudaError_t launch_correct(ls_ctx* ctx, const StepArgs& a);
 
 }  // namespace lsk

@@ -101,22 +101,6 @@ __global__ void k_scatter(int64_t m, int zeta, const int32_t* __restrict__ rows,
   }
 }
 
-__device__ inline void bitonic(uint32_t* s, int P) {
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const uint32_t a = s[i], b = s[ixj];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) { s[i] = b; s[ixj] = a; }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
 // One CTA per sketch row: sort its bucket ascending.  Buckets larger than
 // kSortCap are sorted in global scratch at offset 2*row_ptr[t] (room for the
 // next power of two of the bucket size).
