@@ -613,9 +613,11 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
   batch_plan(probs, np, hp, pl);
   std::vector<int64_t> hoffs(3 * (size_t)np);
   batch_offsets(hp, np, hoffs.data(), hoffs.data() + np, hoffs.data() + 2 * np);
+  std::vector<int> horder((size_t)np);
+  batch_order(hp, np, horder.data());
 
-  auto carve_all = [&](Carve& c, BProb** dP, int64_t** doff3, SketchScratch* sk, BPools* pools, int** alist,
-                       int64_t** aoff, int64_t** cnt) {
+  auto carve_all = [&](Carve& c, BProb** dP, int64_t** doff3, SketchScratch* sk, BPools* pools, int** dorder,
+                       int** alist, int64_t** aoff, int64_t** cnt) {
     *dP = reinterpret_cast<BProb*>(c.take<char>(bprob_bytes() * (size_t)np));
     *doff3 = c.take<int64_t>(3 * (size_t)np);
     *sk = carve_sketch(c, pl.mtotal, pl.dtotal, zeta);
@@ -636,20 +638,22 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
     pools->r_prev = c.take<double>((size_t)pl.mtotal);
     pools->st = c.take<IterState>((size_t)np);
     pools->pstatus = c.take<unsigned int>((size_t)np);
+    *dorder = c.take<int>((size_t)np);
     *alist = c.take<int>((size_t)np);
     *aoff = c.take<int64_t>((size_t)np);
     *cnt = c.take<int64_t>(2);
   };
-  BProb* dP; int64_t* doff3; SketchScratch sk; BPools pools; int* alist; int64_t* aoff; int64_t* cnt;
+  BProb* dP; int64_t* doff3; SketchScratch sk; BPools pools; int* dorder; int* alist; int64_t* aoff; int64_t* cnt;
   Carve probe(nullptr);
-  carve_all(probe, &dP, &doff3, &sk, &pools, &alist, &aoff, &cnt);
+  carve_all(probe, &dP, &doff3, &sk, &pools, &dorder, &alist, &aoff, &cnt);
   ls_status st;
   if ((st = ensure_arena(ctx, probe.off))) return st;
   Carve cc(ctx->arena);
-  carve_all(cc, &dP, &doff3, &sk, &pools, &alist, &aoff, &cnt);
+  carve_all(cc, &dP, &doff3, &sk, &pools, &dorder, &alist, &aoff, &cnt);
   if ((st = reset_status(ctx))) return st;
   CUDA_TRY(ctx, cudaMemcpyAsync(dP, hp, bprob_bytes() * (size_t)np, cudaMemcpyHostToDevice, ctx->stream));
   CUDA_TRY(ctx, cudaMemcpyAsync(doff3, hoffs.data(), sizeof(int64_t) * 3 * np, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(dorder, horder.data(), sizeof(int) * np, cudaMemcpyHostToDevice, ctx->stream));
   CUDA_TRY(ctx, cudaMemsetAsync(pools.pstatus, 0, sizeof(unsigned int) * np, ctx->stream));
   CUDA_TRY(ctx, cudaMemsetAsync(pools.r_prev, 0, sizeof(double) * pl.mtotal, ctx->stream));
   const long long l0 = ctx->launches;
@@ -679,7 +683,7 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
                                     sizeof(double) * (size_t)probs[p].d * (probs[p].n + 1),
                                     cudaMemcpyDeviceToDevice, ctx->stream));
   // factor
-  CUDA_TRY(ctx, launch_b_factor(ctx, dP, pl, pools));
+  CUDA_TRY(ctx, launch_b_factor(ctx, dP, dorder, pl, pools));
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
   for (int p = 0; p < np; ++p)
     if (probs[p].R_out)

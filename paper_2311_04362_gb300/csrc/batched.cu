@@ -249,73 +249,203 @@ __global__ void __launch_bounds__(256) k_b_gather(const BProb* __restrict__ P, c
       const double v1 = __ldg(base + (int64_t)((n1 >> 1) - mo) * stride);
       const double v2 = __ldg(base + (int64_t)((n2 >> 1) - mo) * stride);
       const double v3 = __ldg(base + (int64_t)((n3 >> 1) - mo) * stride);
-      acc = (n0 & 1u) ? acc - v0 : acc + v0;
-      acc = (n1 & 1u) ? acc - v1 : acc + v1;
-      acc = (n2 & 1u) ? acc - v2 : acc + v2;
-      acc = (n3 & 1u) ? acc - v3 : acc + v3;
+      acc = acc + signed_by(v0, n0);
+      acc = acc + signed_by(v1, n1);
+      acc = acc + signed_by(v2, n2);
+      acc = acc + signed_by(v3, n3);
     }
     for (; e < e1; ++e) {
       const uint32_t n0 = __ldg(ent + e);
       const double v0 = __ldg(base + (int64_t)((n0 >> 1) - mo) * stride);
-      acc = (n0 & 1u) ? acc - v0 : acc + v0;
+      acc = acc + signed_by(v0, n0);
     }
     B[t + c * pr.d] = scale * acc;
   }
 }
 
 // ---------------------------------------------------------------- factor
-// One CTA per problem: unblocked Householder QR of B_p (d x (n+1)), reflectors
-// for the first n columns applied to all later columns.
-__global__ void __launch_bounds__(256) k_b_householder(const BProb* __restrict__ P, double* __restrict__ Bpool,
+// One CTA per problem, problems in order of decreasing work (d n^2), blocked
+// Householder QR (LAPACK convention) of B_p = [S A_p, S b_p], d x (n + 1):
+// panels of kHB columns are factored column by column; the panel's
+// reflectors are then applied to the trailing columns at once in compact-WY
+// form, C <- C - V T^T (V^T C), reading C twice per panel instead of twice
+// per column.  The trailing update runs on (row group, column) threads that
+// keep W = V^T C and Y = T^T W for their column in registers while V is
+// staged in shared memory by row chunks.
+static constexpr int kHB = 16;        // panel width
+static constexpr int kHChunk = 64;    // rows of V per shared-memory chunk
+
+__global__ void __launch_bounds__(256, 3) k_b_householder(const BProb* __restrict__ P, const int* __restrict__ order,
+                                                       double* __restrict__ Bpool,
                                                        unsigned int* __restrict__ pstatus) {
-  const BProb pr = P[blockIdx.x];
+  __shared__ double Vs[kHChunk * kHB];
+  __shared__ double Wp[256 * kHB];
+  __shared__ double T[kHB * kHB];
+  __shared__ double Gs[kHB * kHB];
+  __shared__ double taus[kHB];
+  __shared__ double tmp[kHB];
+  __shared__ double s_par[3];
+  __shared__ int s_bad;
+  const int p = order[blockIdx.x];
+  const BProb pr = P[p];
   const int64_t d = pr.d;
   const int n = (int)pr.n;
   double* B = Bpool + pr.boff;
-  __shared__ double s_par[3];
-  __shared__ int s_bad;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = 0; k < n; ++k) {
-    double* col = B + k + (int64_t)k * d;
-    const int64_t len = d - k;
-    double ss = 0.0;
-    for (int64_t i = 1 + threadIdx.x; i < len; i += blockDim.x) ss += col[i] * col[i];
-    ss = cta_sum(ss);
-    if (threadIdx.x == 0) {
-      const double alpha = col[0];
-      const double xnorm = sqrt(ss);
-      double beta, tau, scal;
-      if (xnorm == 0.0) { beta = alpha; tau = 0.0; scal = 1.0; }
-      else {
-        const double h = hypot(alpha, xnorm);
-        beta = (alpha >= 0.0) ? -h : h;
-        tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int k0 = 0; k0 < n; k0 += kHB) {
+    const int w = min(kHB, n - k0);
+    // ---- panel: columns k0 .. k0 + w - 1, unblocked
+    for (int kk = 0; kk < w; ++kk) {
+      const int k = k0 + kk;
+      double* col = B + k + (int64_t)k * d;
+      const int64_t len = d - k;
+      double ss = 0.0;
+      for (int64_t i = 1 + tid; i < len; i += 256) ss += col[i] * col[i];
+      ss = cta_sum(ss);
+      if (tid == 0) {
+        const double alpha = col[0];
+        const double xnorm = sqrt(ss);
+        double beta, tau, scal;
+        if (xnorm == 0.0) { beta = alpha; tau = 0.0; scal = 1.0; }
+        else {
+          const double h = hypot(alpha, xnorm);
+          beta = (alpha >= 0.0) ? -h : h;
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
+        s_par[0] = beta; s_par[1] = tau; s_par[2] = scal;
+        s_bad = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+        taus[kk] = tau;
       }
-      s_par[0] = beta; s_par[1] = tau; s_par[2] = scal;
-      s_bad = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+      __syncthreads();
+      if (s_bad) {
+        if (tid == 0) pstatus[p] |= LS_DEV_RANK;
+        return;
+      }
+      const double tau = s_par[1], scal = s_par[2];
+      if (tau != 0.0)
+        for (int64_t i = 1 + tid; i < len; i += 256) col[i] *= scal;
+      __syncthreads();
+      if (tid == 0) col[0] = s_par[0];
+      if (tau != 0.0) {
+        for (int j = k + 1 + warp; j < k0 + w; j += 8) {
+          double* cj = B + k + (int64_t)j * d;
+          double acc = 0.0;
+          for (int64_t i = lane; i < len; i += 32) acc += ((i == 0) ? 1.0 : col[i]) * cj[i];
+          acc = warp_sum(acc);
+          const double tw = tau * acc;
+          for (int64_t i = lane; i < len; i += 32) cj[i] = cj[i] - tw * ((i == 0) ? 1.0 : col[i]);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (s_bad) {
-      if (threadIdx.x == 0) pstatus[blockIdx.x] |= LS_DEV_RANK;
-      return;
+    const int j0 = k0 + w;                  // first trailing column
+    const int ncols = n + 1 - j0;           // >= 1 (column n is S b)
+    // ---- Gram G[a][b] = v_a^T v_b (a < b) of the panel's reflectors
+    const int npairs = w * (w - 1) / 2;
+    for (int pi = warp; pi < npairs; pi += 8) {
+      int a = 0, rem = pi;
+      while (rem >= w - 1 - a) { rem -= w - 1 - a; ++a; }
+      const int b = a + 1 + rem;
+      const double* va = B + (int64_t)(k0 + a) * d;
+      const double* vb = B + (int64_t)(k0 + b) * d;
+      double acc = 0.0;
+      for (int64_t i = k0 + b + lane; i < d; i += 32) acc += va[i] * ((i == k0 + b) ? 1.0 : vb[i]);
+      acc = warp_sum(acc);
+      if (lane == 0) Gs[a * kHB + b] = acc;
     }
-    const double tau = s_par[1], scal = s_par[2];
-    if (tau != 0.0)
-      for (int64_t i = 1 + threadIdx.x; i < len; i += blockDim.x) col[i] *= scal;
+    if (tid < kHB * kHB) T[tid] = 0.0;
     __syncthreads();
-    if (threadIdx.x == 0) col[0] = s_par[0];
-    if (tau != 0.0) {
-      for (int j = k + 1 + warp; j <= n; j += nw) {
-        double* cj = B + k + (int64_t)j * d;
-        double w = 0.0;
-        for (int64_t i = lane; i < len; i += 32) w += ((i == 0) ? 1.0 : col[i]) * cj[i];
-        w = warp_sum(w);
-        const double tw = tau * w;
-        for (int64_t i = lane; i < len; i += 32) cj[i] = cj[i] - tw * ((i == 0) ? 1.0 : col[i]);
+    // ---- T (upper): T[kk][kk] = tau_kk, T[0:kk, kk] = -tau_kk T[0:kk, 0:kk] G[0:kk, kk]
+    for (int kk = 0; kk < w; ++kk) {
+      if (tid < kk) {
+        double t = 0.0;
+        for (int c = tid; c < kk; ++c) t += T[tid * kHB + c] * Gs[c * kHB + kk];
+        tmp[tid] = -taus[kk] * t;
+      }
+      __syncthreads();
+      if (tid < kk) T[tid * kHB + kk] = tmp[tid];
+      if (tid == 0) T[kk * kHB + kk] = taus[kk];
+      __syncthreads();
+    }
+    // ---- trailing update of columns j0 .. n, rows k0 .. d - 1
+    for (int cb = 0; cb < ncols; cb += 256) {
+      const int nc = min(256, ncols - cb);
+      const int Gr = max(1, 256 / nc);
+      const int g = tid / nc, jl = tid - g * nc;
+      const bool active = g < Gr;
+      double* cj = B + (int64_t)(j0 + cb + jl) * d;
+      double acc[kHB];
+#pragma unroll
+      for (int q = 0; q < kHB; ++q) acc[q] = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t r0 = k0; r0 < d; r0 += kHChunk) {
+          const int h = (int)min((int64_t)kHChunk, d - r0);
+          for (int e = tid; e < h * kHB; e += 256) {
+            const int i = e / kHB, q = e - i * kHB;
+            const int64_t R = r0 + i, dq = k0 + q;
+            double v = 0.0;
+            if (q < w) v = (R < dq) ? 0.0 : (R == dq ? 1.0 : B[R + dq * d]);
+            Vs[e] = v;
+          }
+          __syncthreads();
+          if (active) {
+            const int rpg = (h + Gr - 1) / Gr;
+            const int i0 = g * rpg, i1 = min(h, i0 + rpg);
+            if (pass == 0) {
+              for (int i = i0; i < i1; ++i) {
+                const double c = cj[r0 + i];
+                const double* vr = Vs + i * kHB;
+#pragma unroll
+                for (int q = 0; q < kHB; ++q) acc[q] = fma(vr[q], c, acc[q]);
+              }
+            } else {
+              for (int i = i0; i < i1; ++i) {
+                double c = cj[r0 + i];
+                const double* vr = Vs + i * kHB;
+#pragma unroll
+                for (int q = 0; q < kHB; ++q) c = fma(-vr[q], acc[q], c);
+                cj[r0 + i] = c;
+              }
+            }
+          }
+          __syncthreads();
+        }
+        if (pass == 0) {
+          // W of column jl = sum of the row groups' partials (group order);
+          // then Y = T^T W, handed to every row group through Wp
+          if (active)
+#pragma unroll
+            for (int q = 0; q < kHB; ++q) Wp[(g * nc + jl) * kHB + q] = acc[q];
+          __syncthreads();
+          if (active && g == 0) {
+            double wv[kHB];
+#pragma unroll
+            for (int q = 0; q < kHB; ++q) {
+              double t = 0.0;
+              for (int gg = 0; gg < Gr; ++gg) t += Wp[(gg * nc + jl) * kHB + q];
+              wv[q] = t;
+            }
+#pragma unroll
+            for (int q = 0; q < kHB; ++q) {
+              double y = 0.0;
+#pragma unroll
+              for (int a = 0; a <= q; ++a) y = fma(T[a * kHB + q], wv[a], y);
+              acc[q] = y;
+            }
+          }
+          __syncthreads();
+          if (active && g == 0)
+#pragma unroll
+            for (int q = 0; q < kHB; ++q) Wp[jl * kHB + q] = acc[q];
+          __syncthreads();
+          if (active)
+#pragma unroll
+            for (int q = 0; q < kHB; ++q) acc[q] = Wp[jl * kHB + q];
+          __syncthreads();
+        }
       }
     }
-    __syncthreads();
   }
 }
 
@@ -458,7 +588,7 @@ __global__ void k_b_iter_init(const BProb* __restrict__ P, int np, BPools pl, do
 }
 
 static constexpr int kBThreads = 256;
-static constexpr int kBTileCap = 6144;      // doubles per tile buffer (48 KB)
+static constexpr int kBTileCap = 3840;      // doubles per tile buffer (30 KB): 3 CTAs per SM
 
 // Active problems in index order (alist) and the exclusive prefix of their
 // pass tiles (aoff); cnt[0] = active problems, cnt[1] = their tiles.
@@ -542,7 +672,7 @@ __device__ inline BItem b_locate(const int* __restrict__ alist, const int64_t* _
 }
 
 // Persistent pass over the tiles of the active problems.
-__global__ void __launch_bounds__(kBThreads, 2) k_b_pass(const BProb* __restrict__ P, const int* __restrict__ alist,
+__global__ void __launch_bounds__(kBThreads, 3) k_b_pass(const BProb* __restrict__ P, const int* __restrict__ alist,
                                                          const int64_t* __restrict__ aoff,
                                                          const int64_t* __restrict__ cnt, BPools pl, int max_n,
                                                          unsigned int* __restrict__ status) {
@@ -551,8 +681,8 @@ __global__ void __launch_bounds__(kBThreads, 2) k_b_pass(const BProb* __restrict
   double* xs = buf0 + 2 * kBTileCap;                 // max_n (even)
   double* part1 = xs + ((max_n + 1) & ~1);           // 256
   double* rt = part1 + kBThreads;                    // 256
-  double* q1 = rt + kBThreads;                       // 256: r_j^2
-  double* q2 = q1 + kBThreads;                       // 256: (r_j - r_prev_j)^2
+  double* q1 = rt + kBThreads;                       // 256: r_j
+  double* q2 = q1 + kBThreads;                       // 256: r_j - r_prev_j
   double* gs = q2 + kBThreads;                       // 256: phase-2 group sums
   uint64_t* bar = reinterpret_cast<uint64_t*>(gs + kBThreads);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -614,14 +744,14 @@ __global__ void __launch_bounds__(kBThreads, 2) k_b_pass(const BProb* __restrict
     if (tid < TR) {
       double v1 = 0.0, v2 = 0.0;
       if (tid < rows) {
-        double dot = 0.0;
-        for (int sidx = 0; sidx < S; ++sidx) dot += part1[sidx * TR + tid];
+        double dot = part1[tid];
+        for (int sidx = 1; sidx < S; ++sidx) dot += part1[sidx * TR + tid];
         const double rj = __ldg(pr.b + row0 + tid) - dot;
         const double dl = rj - rp[tid];
         rp[tid] = rj;
         rt[tid] = rj;
-        v1 = rj * rj;
-        v2 = dl * dl;
+        v1 = rj;
+        v2 = dl;
       }
       q1[tid] = v1;
       q2[tid] = v2;
@@ -648,7 +778,7 @@ __global__ void __launch_bounds__(kBThreads, 2) k_b_pass(const BProb* __restrict
     if (warp < 2) {
       const double* q = warp ? q2 : q1;
       double v = 0.0;
-      for (int r = lane; r < TR; r += 32) v += q[r];
+      for (int r = lane; r < TR; r += 32) v = fma(q[r], q[r], v);
       v = warp_sum(v);
       if (lane == 0) out[n + warp] = v;
     }
@@ -830,8 +960,16 @@ cudaError_t launch_b_csr(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools) {
-  k_b_householder<<<pl.np, 256, 0, ctx->stream>>>(dP, pools.B, pools.pstatus);
+void batch_order(const BProb* P, int np, int* order) {
+  for (int p = 0; p < np; ++p) order[p] = p;
+  std::stable_sort(order, order + np, [&](int a, int b) {
+    return (double)P[a].d * P[a].n * P[a].n > (double)P[b].d * P[b].n * P[b].n;
+  });
+}
+
+cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const int* dorder, const BatchPlan& pl,
+                            const BPools& pools) {
+  k_b_householder<<<pl.np, 256, 0, ctx->stream>>>(dP, dorder, pools.B, pools.pstatus);
   ++ctx->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -205,6 +205,13 @@ __device__ inline bool grid_sync(const GridBar& gb, unsigned int nblocks) {
   return s_ok != 0;
 }
 
+// v with its sign flipped when bit 0 of en is set (an integer XOR on the sign
+// bit), so that acc + signed_by(v, en) is acc + v or acc - v exactly (IEEE
+// subtraction is addition of the negation) with a single FP64 add.
+__device__ inline double signed_by(double v, uint32_t en) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(en & 1u) << 63));
+}
+
 // ------------------------------------------------------------ reductions
 // Block-wide bitonic sort of s[0..P) ascending (P a power of two; every
 // thread of the block calls it).
@@ -367,7 +374,9 @@ cudaError_t launch_b_sketch_indices(ls_ctx* ctx, const BProb* dP, const int64_t*
                                     int zeta, int32_t* rows, uint32_t* signs);
 cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* dwoffs, const BatchPlan& pl,
                             const int64_t* row_ptr, const uint32_t* ent, double scale, double* Bpool);
-cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools);
+void batch_order(const BProb* P, int np, int* order);
+cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const int* dorder, const BatchPlan& pl,
+                            const BPools& pools);
 cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools,
                                double gamma, double rho, double alpha, double beta);
 cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int* alist,

@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(256) k_gather_add(const double* __restrict__ A
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (en[u] & 1u) { a0 = a0 - v[u].x; a1 = a1 - v[u].y; }
-        else { a0 = a0 + v[u].x; a1 = a1 + v[u].y; }
+        a0 = a0 + signed_by(v[u].x, en[u]);
+        a1 = a1 + signed_by(v[u].y, en[u]);
       }
     }
     for (; e < e1; ++e) {
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(256) k_gather_add(const double* __restrict__ A
       double2 v = make_double2(0.0, 0.0);
       if (pair) v = __ldg(reinterpret_cast<const double2*>(p));
       else if (single) v.x = __ldg(p);
-      if (en & 1u) { a0 = a0 - v.x; a1 = a1 - v.y; }
-      else { a0 = a0 + v.x; a1 = a1 + v.y; }
+      a0 = a0 + signed_by(v.x, en);
+      a1 = a1 + signed_by(v.y, en);
     }
     if (single) B[t + c * ldb] = scale * a0;
     if (pair) B[t + (c + 1) * ldb] = scale * a1;
@@ -183,7 +183,7 @@ __global__ void k_gather_b(const double* __restrict__ b, int64_t d, const int64_
   for (int64_t e = row_ptr[t]; e < row_ptr[t + 1]; ++e) {
     const uint32_t en = __ldg(ent + e);
     const double v = __ldg(b + (en >> 1));
-    if (en & 1u) acc = acc - v; else acc = acc + v;
+    acc = acc + signed_by(v, en);
   }
   Bcol[t] = scale * acc;
 }
