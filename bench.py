@@ -194,6 +194,8 @@ def main():
                     help="pass / sketch: only the fused residual/gradient pass, or only the sketch B = S[A b], "
                          "on an m x 1000 problem (for ncu captures)")
     ap.add_argument("--m", type=int, default=200_000, help="rows for --case pass")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-problems timing")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) sweep")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -314,6 +316,14 @@ def main():
                                "fe": float(torch.linalg.norm(xv - xtrue) / torch.linalg.norm(xtrue)),
                                "status": ls.STATUS_NAMES[st_v]}
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_case(ctx, stream, args, pg, world, rank)
+
+    serving = None
+    if not args.no_serving:
+        serving = serving_case(ctx, args)
+
     fe_qr = None
     if args.check_qr and rank == 0:
         import oracle
@@ -346,6 +356,8 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "accuracy": {"fe": fe, "status": statuses, "iters": iters, **(fe_qr or {})},
             "variants_app_b": variants,
+            "batched": batched,
+            "serving": serving,
             "phase_ms": {"sketch": statistics.mean(i.ms_sketch for _, i in infos),
                          "factor": statistics.mean(i.ms_factor for _, i in infos),
                          "iterate": statistics.mean(i.ms_iterate for _, i in infos)},
@@ -356,6 +368,147 @@ def main():
     ctx.close()
     if pg:
         pg.destroy_process_group()
+
+
+def batched_case(ctx, stream, args, pg, world, rank):
+    """4096 independent uneven problems (problems.BATCH) solved by one
+    ls_solve_batched call per step; solves/s over the whole batch, timed with
+    CUDA events on the launching stream.  Acceptance: the fraction of problems
+    whose forward error is within 10x that of a Householder-QR solve (geqrf
+    through torch) -- Algorithm 2 as stated and with the App. B momentum
+    weights (e = sqrt(n/d) = sqrt(1/20) for every problem)."""
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    import problems
+
+    cfg = problems.BATCH
+    shapes = problems.batch_shapes(**cfg)
+    probs = problems.make_batch_torch(shapes)
+    nprob = len(probs)
+    fe_qr = []
+    for p in probs:
+        n = p["n"]
+        Q, R = torch.linalg.qr(p["A"][:, :n])
+        xq = torch.linalg.solve_triangular(R, (Q.T @ p["b"])[:, None], upper=True)[:, 0]
+        fe_qr.append(float(torch.linalg.norm(xq - p["x_true"]) / torch.linalg.norm(p["x_true"])))
+        del Q, R
+    out = {"workload": "4096 uneven FP64 problems: m log-uniform in [500, 20000], n log-uniform in [10, 200], "
+                       "m >= 20n, kappa log-uniform in [1e2, 1e12], ||r|| log-uniform in [1e-10, 1e-2], d = 20n, "
+                       "zeta = 8, Philox seed = problem index, q <= 100 with the Sec. 3.3 stopping rule",
+           "problems": nprob, "sum_m": int(sum(s["m"] for s in shapes)),
+           "A_bytes": int(sum(8 * p["m"] * p["lda"] for p in probs))}
+    steps = max(1, args.steps // 2)
+    for name, opts in (("basic", ls.default_opts()), ("momentum", ls.momentum_opts(1, 20))):
+        ctx.ls_solve_batched(probs, cfg["zeta"], cfg["q"], opts)      # warm
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            infos = ctx.ls_solve_batched(probs, cfg["zeta"], cfg["q"], opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+        fe = [float(torch.linalg.norm(p["x"] - p["x_true"]) / torch.linalg.norm(p["x_true"])) for p in probs]
+        ok = sum(1 for a, q_ in zip(fe, fe_qr) if a <= 10 * q_)
+        held = sum(1 for i in infos if i.stop_reason == 0)
+        its = [i.iters for i in infos]
+        out[name] = {"value": job_throughput(world, steps * nprob, ms), "unit": UNIT,
+                     "ms_per_batch": ms / steps, "steps": steps, "alpha": opts.alpha, "beta": opts.beta,
+                     "accept_10x_qr": ok / nprob, "rule_held": held / nprob,
+                     "iters_mean": sum(its) / nprob, "iters_max": max(its),
+                     "phase_ms": {"sketch": infos[0].ms_sketch, "factor": infos[0].ms_factor,
+                                  "iterate": infos[0].ms_iterate},
+                     "gpu_launches_per_batch": infos[0].launches}
+    del probs
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_case(ctx, args):
+    """Continuous batching (ls_server_*): Poisson arrival streams at each rate
+    of problems.SERVE, requests drawn from a pool of problems resident in HBM,
+    admission within a 150 GB budget (each request counts its A, b, x and
+    workspace).  Per rate: completed solves/s over the span from the first
+    arrival to the last completion, p50/p99 latency from arrival (host clock)
+    to the poll that returned the request, and the fraction of requests whose
+    forward error is within 10x that of a Householder-QR solve of their
+    problem."""
+    import numpy as np
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    import problems
+
+    cfg = problems.SERVE
+    shapes = problems.batch_shapes(**cfg)
+    pool = problems.make_batch_torch(shapes)
+    fe_qr = []
+    for p in pool:
+        n = p["n"]
+        Q, R = torch.linalg.qr(p["A"][:, :n])
+        xq = torch.linalg.solve_triangular(R, (Q.T @ p["b"])[:, None], upper=True)[:, 0]
+        fe_qr.append(float(torch.linalg.norm(xq - p["x_true"]) / torch.linalg.norm(p["x_true"])))
+        del Q, R
+    torch.cuda.synchronize()
+    nreq = cfg["requests_per_rate"]
+    xbuf = torch.empty((nreq, max(p["n"] for p in pool)), dtype=torch.float64, device="cuda")
+    srv = ls.Server(ctx, 2048, 512, 48 * 2**30, cfg["budget_bytes"], cfg["zeta"], cfg["q"])
+    out = {"workload": "Poisson arrivals of FP64 requests drawn from a pool of 96 problems: n log-uniform in "
+                       "[20, 500], m log-uniform in [max(1000, 20n), 5e5], kappa log-uniform in [1e2, 1e10], "
+                       "||r|| log-uniform in [1e-8, 1e-2], d = 20n, zeta = 8, q <= 100; 150 GB admission budget",
+           "pool_A_bytes": int(sum(8 * p["m"] * p["lda"] for p in pool)), "rates": []}
+    try:
+        for rate in cfg["rates"]:
+            arr = problems.poisson_arrivals(rate, nreq, cfg["seed"])
+            rng = np.random.default_rng(np.random.SeedSequence([cfg["seed"], int(rate), 0x9001]))
+            pick = rng.integers(0, len(pool), nreq)
+            tick = {}
+            done_t = {}
+            infos = {}
+            i = 0
+            peak = 0
+            steps = 0
+            t0 = time.perf_counter()
+            while len(done_t) < nreq:
+                now = time.perf_counter() - t0
+                while i < nreq and arr[i] <= now:
+                    p = pool[pick[i]]
+                    req = dict(p, x=xbuf[i, :p["n"]], seed=i)
+                    tick[srv.ls_server_submit(req)] = i
+                    i += 1
+                st = srv.ls_server_get_stats()
+                if st["inflight"] + st["queued"] == 0:
+                    if i < nreq:
+                        while time.perf_counter() - t0 < arr[i]:
+                            pass
+                    continue
+                srv.ls_server_step()
+                steps += 1
+                peak = max(peak, st["inflight"])
+                tnow = time.perf_counter() - t0
+                for t, info in srv.ls_server_poll():
+                    done_t[tick[t]] = tnow
+                    infos[tick[t]] = info
+            lat = np.array([done_t[k] - arr[k] for k in range(nreq)]) * 1e3
+            span = max(done_t.values()) - arr[0]
+            ok = 0
+            for k in range(nreq):
+                p = pool[pick[k]]
+                fe = float(torch.linalg.norm(xbuf[k, :p["n"]] - p["x_true"]) / torch.linalg.norm(p["x_true"]))
+                ok += fe <= 10 * fe_qr[pick[k]]
+            out["rates"].append({"rate": rate, "requests": nreq, "solves_per_s": nreq / span,
+                                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                 "accept_10x_qr": ok / nreq,
+                                 "rule_held": sum(1 for v in infos.values() if v.stop_reason == 0) / nreq,
+                                 "peak_inflight": peak, "steps": steps})
+    finally:
+        srv.close()
+    del pool, xbuf
+    torch.cuda.empty_cache()
+    return out
 
 
 def pass_case(args):

@@ -205,6 +205,52 @@ LS_API ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t
 LS_API ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int nprob, int zeta, int q,
                                   const ls_opts* opts, ls_info* infos);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching (no counterpart in the paper, which solves one problem
+ * at a time): requests are queued by ls_server_submit, admitted in arrival
+ * order while the admission budget allows, and every in-flight request
+ * advances by one iteration of Algorithm 2 per ls_server_step.  Each admitted
+ * request is sketched, factored and started exactly as ls_solve_batched does
+ * it, so its result is bit-identical to solving it alone.  The server runs on
+ * its own CUDA stream: the caller must have finished writing A and b before
+ * ls_server_submit, and must not touch x until the request is returned by
+ * ls_server_poll.  One thread at a time per server. */
+typedef struct ls_server ls_server;
+typedef struct {
+    int64_t inflight;               /* admitted, not finished */
+    int64_t queued;                 /* submitted, not admitted */
+    int64_t completed;
+    int64_t steps;                  /* iteration steps run */
+    size_t admitted_bytes;          /* budget in use (resident A, b, x + workspace) */
+    size_t workspace_bytes_used;    /* arena bytes in use */
+} ls_server_stats;
+
+/* Bytes a request counts against the admission budget: its A (m x lda), b,
+ * x and the server workspace (sketch d x (n+1), R and R^T, eight n-vectors,
+ * pass partials, previous residual).  0 for invalid sizes. */
+LS_API size_t ls_server_request_bytes(int64_t m, int64_t n, int64_t lda, int64_t d);
+
+/* Create a server on ctx's device.  max_inflight: slots; max_n (<= 1024):
+ * largest n accepted; workspace_bytes: device arena for the workspaces
+ * (allocated here); admit_bytes: admission budget (0: workspace_bytes);
+ * zeta, q, opts: as for ls_solve_ex (opts may be NULL).  Errors: LS_EINVAL,
+ * LS_ENOMEM, LS_ECUDA (text in ls_last_error(ctx)). */
+LS_API ls_status ls_server_create(ls_ctx* ctx, int max_inflight, int64_t max_n, size_t workspace_bytes,
+                                  size_t admit_bytes, int zeta, int q, const ls_opts* opts, ls_server** out);
+LS_API ls_status ls_server_destroy(ls_server* srv);
+/* Queue a request (device pointers as in ls_problem; B_out and R_out are
+ * ignored; d <= 12288).  *ticket identifies it in ls_server_poll.  LS_ENOMEM
+ * when the request alone exceeds the budget or the arena. */
+LS_API ls_status ls_server_submit(ls_server* srv, const ls_problem* prob, int64_t* ticket);
+/* Admit what fits, then one iteration of every in-flight request; returns
+ * after the step has finished on the device.  *n_done (may be NULL): requests
+ * finished in this call. */
+LS_API ls_status ls_server_step(ls_server* srv, int* n_done);
+/* Move up to cap finished requests out: tickets[i] and infos[i] (either may
+ * be NULL); *n_out set to the number returned. */
+LS_API ls_status ls_server_poll(ls_server* srv, int64_t* tickets, ls_info* infos, int cap, int* n_out);
+LS_API ls_status ls_server_get_stats(ls_server* srv, ls_server_stats* out);
+
 /* ls_solve with iteration options (stopping rule constants, extra updates,
  * damping / momentum of App. B); opts may be NULL for the defaults. */
 LS_API ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n,

@@ -48,6 +48,11 @@ class ls_problem(C.Structure):
                 ("R_out", C.c_void_p)]
 
 
+class ls_server_stats(C.Structure):
+    _fields_ = [("inflight", C.c_int64), ("queued", C.c_int64), ("completed", C.c_int64), ("steps", C.c_int64),
+                ("admitted_bytes", C.c_size_t), ("workspace_bytes_used", C.c_size_t)]
+
+
 _lib = None
 
 
@@ -93,6 +98,20 @@ def lib():
     L.ls_opts_momentum.argtypes = [C.POINTER(ls_opts), I64, I64]
     L.ls_solve_batched.argtypes = [P, C.POINTER(ls_problem), I, I, I, C.POINTER(ls_opts), C.POINTER(ls_info)]
     L.ls_solve_batched.restype = S
+    L.ls_server_request_bytes.argtypes = [I64, I64, I64, I64]
+    L.ls_server_request_bytes.restype = C.c_size_t
+    L.ls_server_create.argtypes = [P, I, I64, C.c_size_t, C.c_size_t, I, I, C.POINTER(ls_opts), C.POINTER(P)]
+    L.ls_server_create.restype = S
+    L.ls_server_destroy.argtypes = [P]
+    L.ls_server_destroy.restype = S
+    L.ls_server_submit.argtypes = [P, C.POINTER(ls_problem), C.POINTER(C.c_int64)]
+    L.ls_server_submit.restype = S
+    L.ls_server_step.argtypes = [P, C.POINTER(I)]
+    L.ls_server_step.restype = S
+    L.ls_server_poll.argtypes = [P, P, C.POINTER(ls_info), I, C.POINTER(I)]
+    L.ls_server_poll.restype = S
+    L.ls_server_get_stats.argtypes = [P, C.POINTER(ls_server_stats)]
+    L.ls_server_get_stats.restype = S
     L.ls_residual_gradient_noalloc.argtypes = [P, P, I64, I64, I64, P, P, P, P, P, P]
     L.ls_residual_gradient_noalloc.restype = S
     _lib = L
@@ -231,6 +250,65 @@ class Context:
         self._check(lib().ls_solve_batched(self._h, arr, len(probs), zeta, q,
                                            C.byref(opts) if opts is not None else None, infos))
         return infos
+
+
+def server_request_bytes(m, n, lda, d) -> int:
+    return int(lib().ls_server_request_bytes(m, n, lda, d))
+
+
+class Server:
+    """Continuous-batching server (ls_server_*): submit requests, step, poll.
+    Runs on its own CUDA stream; A and b must be ready before submit and x is
+    final once the request comes back from poll."""
+
+    def __init__(self, ctx: Context, max_inflight: int, max_n: int, workspace_bytes: int, admit_bytes: int = 0,
+                 zeta: int = 8, q: int = 100, opts: ls_opts | None = None):
+        self._ctx = ctx
+        self._h = C.c_void_p()
+        st = lib().ls_server_create(ctx.handle, max_inflight, max_n, workspace_bytes, admit_bytes, zeta, q,
+                                    C.byref(opts) if opts is not None else None, C.byref(self._h))
+        ctx._check(st)
+
+    def close(self):
+        if self._h:
+            lib().ls_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def ls_server_submit(self, prob: dict) -> int:
+        p = ls_problem(_ptr(prob["A"]), _ptr(prob["b"]), _ptr(prob["x"]), prob["m"], prob["n"], prob["lda"],
+                       prob["d"], prob.get("seed", 0), None, None)
+        t = C.c_int64()
+        self._ctx._check(lib().ls_server_submit(self._h, C.byref(p), C.byref(t)))
+        return t.value
+
+    def ls_server_step(self) -> int:
+        nd = C.c_int()
+        self._ctx._check(lib().ls_server_step(self._h, C.byref(nd)))
+        return nd.value
+
+    def ls_server_poll(self, cap: int = 4096):
+        tickets = (C.c_int64 * cap)()
+        infos = (ls_info * cap)()
+        n = C.c_int()
+        self._ctx._check(lib().ls_server_poll(self._h, tickets, infos, cap, C.byref(n)))
+        return [(tickets[i], ls_info.from_buffer_copy(infos[i])) for i in range(n.value)]
+
+    def ls_server_get_stats(self) -> dict:
+        st = ls_server_stats()
+        self._ctx._check(lib().ls_server_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
 
 
 def solve(A, b, d=None, zeta=8, q=100, seed=0, ctx: Context | None = None):

@@ -614,7 +614,8 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
   std::vector<int64_t> hoffs(3 * (size_t)np);
   batch_offsets(hp, np, hoffs.data(), hoffs.data() + np, hoffs.data() + 2 * np);
   std::vector<int> horder((size_t)np);
-  batch_order(hp, np, horder.data());
+  const int csize = b_qr_cluster_size(ctx);
+  const int nsmall = batch_order(hp, np, horder.data(), csize > 0);
 
   auto carve_all = [&](Carve& c, BProb** dP, int64_t** doff3, SketchScratch* sk, BPools* pools, int** dorder,
                        int** alist, int64_t** aoff, int64_t** cnt) {
@@ -623,15 +624,9 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
     *sk = carve_sketch(c, pl.mtotal, pl.dtotal, zeta);
     pools->B = c.take<double>((size_t)pl.btotal);
     pools->R = c.take<double>((size_t)pl.rtotal);
-    pools->Rt = c.take<double>((size_t)pl.rtotal);
-    pools->inv_diag = c.take<double>((size_t)pl.vtotal);
-    pools->x_prev = c.take<double>((size_t)pl.vtotal);
-    pools->y = c.take<double>((size_t)pl.vtotal);
-    pools->dvec = c.take<double>((size_t)pl.vtotal);
-    pools->work = c.take<double>((size_t)pl.vtotal);
-    pools->v = c.take<double>((size_t)pl.vtotal);
-    pools->w = c.take<double>((size_t)pl.vtotal);
-    pools->xi = c.take<double>((size_t)pl.vtotal);
+    pools->V = c.take<double>((size_t)pl.vtotal);
+    pools->done_rec = nullptr;
+    pools->done_count = nullptr;
     pools->slots = c.take<double>(64 * (size_t)np);
     pools->est = c.take<double>(2 * (size_t)np);
     pools->part = c.take<double>((size_t)pl.ptotal);
@@ -641,7 +636,7 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
     *dorder = c.take<int>((size_t)np);
     *alist = c.take<int>((size_t)np);
     *aoff = c.take<int64_t>((size_t)np);
-    *cnt = c.take<int64_t>(2);
+    *cnt = c.take<int64_t>(4);
   };
   BProb* dP; int64_t* doff3; SketchScratch sk; BPools pools; int* dorder; int* alist; int64_t* aoff; int64_t* cnt;
   Carve probe(nullptr);
@@ -683,7 +678,7 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
                                     sizeof(double) * (size_t)probs[p].d * (probs[p].n + 1),
                                     cudaMemcpyDeviceToDevice, ctx->stream));
   // factor
-  CUDA_TRY(ctx, launch_b_factor(ctx, dP, dorder, pl, pools));
+  CUDA_TRY(ctx, launch_b_factor2(ctx, dP, dorder, nsmall, dorder + nsmall, np - nsmall, csize, np, nullptr, pools));
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
   for (int p = 0; p < np; ++p)
     if (probs[p].R_out)
@@ -691,13 +686,13 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
                                     sizeof(double) * (size_t)probs[p].n * probs[p].n, cudaMemcpyDeviceToDevice,
                                     ctx->stream));
   // iterate
-  CUDA_TRY(ctx, launch_b_iter_init(ctx, dP, pl, pools, o.gamma, o.rho, o.alpha, o.beta));
-  CUDA_TRY(ctx, launch_b_compact(ctx, dP, pl, pools, alist, aoff, cnt));
+  CUDA_TRY(ctx, launch_b_iter_init(ctx, dP, np, nullptr, pools, o.gamma, o.rho, o.alpha, o.beta));
+  CUDA_TRY(ctx, launch_b_compact(ctx, dP, np, pools, alist, aoff, cnt));
   int64_t* hcnt = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(ctx->h_pinned) + 2048);
   for (int i = 0; i < q; ++i) {
-    CUDA_TRY(ctx, launch_b_pass(ctx, dP, alist, aoff, cnt, pl, pools));
-    CUDA_TRY(ctx, launch_b_step(ctx, dP, pl, pools, o.use_stop, o.extra_iters));
-    CUDA_TRY(ctx, launch_b_compact(ctx, dP, pl, pools, alist, aoff, cnt));
+    CUDA_TRY(ctx, launch_b_pass(ctx, dP, alist, aoff, cnt, pl.max_n, pl.ttotal, pools));
+    CUDA_TRY(ctx, launch_b_step(ctx, dP, alist, cnt, np, pools, o.use_stop, o.extra_iters, q));
+    CUDA_TRY(ctx, launch_b_compact(ctx, dP, np, pools, alist, aoff, cnt));
     if ((i & 7) == 7 && i + 1 < q) {
       CUDA_TRY(ctx, cudaMemcpyAsync(hcnt, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
       CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -720,7 +715,7 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
       std::memset(&in, 0, sizeof in);
       const IterState& s = hst[p];
       in.iters = s.iter;
-      in.stop_reason = s.stop_reason == 4 ? 4 : (s.done ? (s.nonfinite ? 3 : 0) : (o.use_stop ? 1 : 2));
+      in.stop_reason = s.done ? s.stop_reason : (o.use_stop ? 1 : 2);
       in.res_norm = s.rnorm;
       in.step_norm = s.dnorm;
       in.normest = hest[2 * p];

@@ -30,24 +30,7 @@
 
 namespace lsk {
 
-struct BProb {
-  const double* A; const double* b; double* x;
-  int64_t m, n, lda, d;
-  uint64_t seed;
-  int64_t moff;      // sum of m over earlier problems (flattened columns of S)
-  int64_t doff;      // sum of d (buckets)
-  int64_t boff;      // sum of d (n + 1) (B pool)
-  int64_t roff;      // sum of n^2 (R, Rt pools)
-  int64_t voff;      // sum of n (vector pools)
-  int64_t toff;      // sum of gather warps (k_b_gather)
-  int64_t poff;      // sum of tiles (n + 2) (partials)
-  int tr;            // rows per pass tile
-  int tiles;         // pass tiles
-  int ss;            // shared-memory row stride of a tile (doubles, = 2 mod 4)
-  int S;             // column chunks per row in the row-dot phase (S * tr <= 256)
-  int rowcopy;       // 1: one bulk copy per row (lda != ss), 0: one per tile
-  int gw;            // gather lanes per bucket (32, 16, 8 or 4)
-};
+
 
 size_t bprob_bytes() { return sizeof(BProb); }
 int64_t batch_boff(const BProb* P, int p) { return P[p].boff; }
@@ -64,6 +47,23 @@ __device__ inline int find_problem(const int64_t* offs, int np, int64_t g) {
     if (offs[mid] <= g) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+enum { V_INVD = 0, V_XPREV, V_Y, V_D, V_WORK, V_V, V_W, V_XI, V_COUNT };
+__device__ inline double* bvec(const BPools& pl, const BProb& pr, int k) {
+  return pl.V + pr.voff + (int64_t)k * pr.n;
+}
+__device__ inline double* bR(const BPools& pl, const BProb& pr) { return pl.R + pr.roff; }
+__device__ inline double* bRt(const BPools& pl, const BProb& pr) { return pl.R + pr.roff + pr.n * pr.n; }
+
+// Completion record (server mode): the finished slot and its outcome.
+__device__ inline void b_record_done(const BPools& pl, int p, const IterState& s) {
+  if (!pl.done_count) return;
+  const unsigned int pos = atomicAdd(pl.done_count, 1u);
+  BDone r;
+  r.slot = p; r.iters = s.iter; r.stop_reason = s.stop_reason; r.pad = 0;
+  r.res_norm = s.rnorm; r.step_norm = s.dnorm; r.normest = s.normest; r.condest = s.condest;
+  pl.done_rec[pos] = r;
 }
 
 // ---------------------------------------------------------------- sketch
@@ -449,24 +449,260 @@ __global__ void __launch_bounds__(256, 3) k_b_householder(const BProb* __restric
   }
 }
 
-// R_p, Rt_p, 1/diag(R_p) for every problem (grid-stride over all entries of all problems).
-__global__ void k_b_prepare_R(const BProb* __restrict__ P, int np, const double* __restrict__ Bpool,
-                              double* __restrict__ Rpool, double* __restrict__ Rtpool, double* __restrict__ invd,
-                              unsigned int* __restrict__ pstatus) {
-  for (int p = blockIdx.x; p < np; p += gridDim.x) {
+// One thread-block cluster per problem (large n): the same blocked
+// compact-WY Householder QR as k_b_householder with the rows of B_p split
+// into contiguous slices, one per CTA of the cluster.  Each reduction over
+// rows (a column norm, the panel's dot products, the Gram matrix of the
+// panel's reflectors, W = V^T C) is a per-CTA partial in shared memory,
+// summed by every CTA over the cluster in CTA order through distributed
+// shared memory after a cluster barrier; every CTA then takes the same
+// reflector and T, and updates its own rows.  Two cluster barriers per
+// column, two per panel.
+static constexpr int kCQMaxN = 512;                    // widest problem (ncols <= kCQMaxN + 1)
+static constexpr int kCQMinN = 256;                    // narrower problems factor on one CTA
+static constexpr int kCQW = kHB * (kCQMaxN + 8);       // doubles of one W / Y table
+
+__global__ void __launch_bounds__(256, 1) k_b_qr_cluster(const BProb* __restrict__ P, const int* __restrict__ list,
+                                                         double* __restrict__ Bpool,
+                                                         unsigned int* __restrict__ pstatus) {
+  extern __shared__ __align__(16) double cq[];
+  double* Wc = cq;                         // this CTA's partial W (column-major by 16), read by the cluster
+  double* Ys = Wc + kCQW;                  // Y = T^T W for all trailing columns
+  double* Gq = Ys + kCQW;                  // row-group partials (256 x 16)
+  double* Vs = Gq + 256 * kHB;             // V chunk (kHChunk x 16)
+  __shared__ double red_ss[2], red_alpha[2], red_dot[2][kHB], Gp[kHB * kHB];
+  __shared__ double T[kHB * kHB], Gs[kHB * kHB], taus[kHB], tmp[kHB], s_par[3];
+  __shared__ int s_bad;
+  const uint32_t rank = cluster_rank(), C = cluster_nctas();
+  const int p = list[blockIdx.x / C];
+  const BProb pr = P[p];
+  const int64_t d = pr.d;
+  const int n = (int)pr.n;
+  double* B = Bpool + pr.boff;
+  const int64_t h = (d + C - 1) / C;
+  const int64_t rlo = min(d, (int64_t)rank * h), rhi = min(d, rlo + h);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int k0 = 0; k0 < n; k0 += kHB) {
+    const int w = min(kHB, n - k0);
+    for (int kk = 0; kk < w; ++kk) {
+      const int k = k0 + kk, par = kk & 1;
+      double* col = B + (int64_t)k * d;
+      // ---- column norm below the diagonal, reflector (identical in every CTA)
+      double ss = 0.0;
+      for (int64_t i = max(rlo, (int64_t)k + 1) + tid; i < rhi; i += 256) ss += col[i] * col[i];
+      ss = cta_sum(ss);
+      const uint32_t owner = (uint32_t)(k / h);
+      if (tid == 0) {
+        red_ss[par] = ss;
+        if (owner == rank) red_alpha[par] = col[k];
+      }
+      cluster_sync();
+      if (tid == 0) {
+        double t = 0.0;
+        for (uint32_t c = 0; c < C; ++c) t += ld_cluster_f64(map_shared(&red_ss[par], c));
+        const double alpha = ld_cluster_f64(map_shared(&red_alpha[par], owner));
+        const double xnorm = sqrt(t);
+        double beta, tau, scal;
+        if (xnorm == 0.0) { beta = alpha; tau = 0.0; scal = 1.0; }
+        else {
+          const double hh = hypot(alpha, xnorm);
+          beta = (alpha >= 0.0) ? -hh : hh;
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
+        s_par[0] = beta; s_par[1] = tau; s_par[2] = scal;
+        s_bad = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+        taus[kk] = tau;
+      }
+      __syncthreads();
+      if (s_bad) {                               // the same decision in every CTA
+        if (rank == 0 && tid == 0) pstatus[p] |= LS_DEV_RANK;
+        cluster_sync();                          // no CTA leaves while others read its shared memory
+        return;
+      }
+      const double tau = s_par[1], scal = s_par[2];
+      if (tau != 0.0)
+        for (int64_t i = max(rlo, (int64_t)k + 1) + tid; i < rhi; i += 256) col[i] *= scal;
+      __syncthreads();
+      if (tid == 0 && owner == rank) col[k] = s_par[0];
+      // ---- the reflector applied to the rest of the panel
+      for (int j = k + 1 + warp; j < k0 + w; j += 8) {
+        const double* cj = B + (int64_t)j * d;
+        double acc = 0.0;
+        if (tau != 0.0)
+          for (int64_t i = max(rlo, (int64_t)k) + lane; i < rhi; i += 32) acc += ((i == k) ? 1.0 : col[i]) * cj[i];
+        acc = warp_sum(acc);
+        if (lane == 0) red_dot[par][j - k0] = acc;
+      }
+      cluster_sync();
+      if (tau != 0.0) {
+        for (int j = k + 1 + warp; j < k0 + w; j += 8) {
+          double dot = 0.0;
+          if (lane == 0)
+            for (uint32_t c = 0; c < C; ++c) dot += ld_cluster_f64(map_shared(&red_dot[par][j - k0], c));
+          dot = __shfl_sync(0xffffffffu, dot, 0);
+          const double tw = tau * dot;
+          double* cj = B + (int64_t)j * d;
+          for (int64_t i = max(rlo, (int64_t)k) + lane; i < rhi; i += 32) cj[i] = cj[i] - tw * ((i == k) ? 1.0 : col[i]);
+        }
+      }
+      __syncthreads();
+    }
+    const int j0 = k0 + w;
+    const int ncols = n + 1 - j0;
+    // ---- Gram of the panel's reflectors over this CTA's rows, summed over the cluster
+    const int npairs = w * (w - 1) / 2;
+    for (int pi = warp; pi < npairs; pi += 8) {
+      int a = 0, rem = pi;
+      while (rem >= w - 1 - a) { rem -= w - 1 - a; ++a; }
+      const int b = a + 1 + rem;
+      const double* va = B + (int64_t)(k0 + a) * d;
+      const double* vb = B + (int64_t)(k0 + b) * d;
+      double acc = 0.0;
+      for (int64_t i = max(rlo, (int64_t)(k0 + b)) + lane; i < rhi; i += 32)
+        acc += va[i] * ((i == k0 + b) ? 1.0 : vb[i]);
+      acc = warp_sum(acc);
+      if (lane == 0) Gp[a * kHB + b] = acc;
+    }
+    cluster_sync();
+    for (int e = tid; e < kHB * kHB; e += 256) {
+      const int a = e / kHB, b = e - a * kHB;
+      double g = 0.0;
+      if (a < b && b < w)
+        for (uint32_t c = 0; c < C; ++c) g += ld_cluster_f64(map_shared(&Gp[e], c));
+      Gs[e] = g;
+      T[e] = 0.0;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < w; ++kk) {
+      if (tid < kk) {
+        double t = 0.0;
+        for (int c = tid; c < kk; ++c) t += T[tid * kHB + c] * Gs[c * kHB + kk];
+        tmp[tid] = -taus[kk] * t;
+      }
+      __syncthreads();
+      if (tid < kk) T[tid * kHB + kk] = tmp[tid];
+      if (tid == 0) T[kk * kHB + kk] = taus[kk];
+      __syncthreads();
+    }
+    // ---- W = V^T C over this CTA's rows (row groups x columns), all column blocks
+    const int64_t lo = max(rlo, (int64_t)k0);
+    for (int cb = 0; cb < ncols; cb += 256) {
+      const int nc = min(256, ncols - cb);
+      const int Gr = max(1, 256 / nc);
+      const int g = tid / nc, jl = tid - g * nc;
+      const bool active = g < Gr;
+      const double* cj = B + (int64_t)(j0 + cb + jl) * d;
+      double acc[kHB];
+#pragma unroll
+      for (int q = 0; q < kHB; ++q) acc[q] = 0.0;
+      for (int64_t r0 = lo; r0 < rhi; r0 += kHChunk) {
+        const int hgt = (int)min((int64_t)kHChunk, rhi - r0);
+        for (int e = tid; e < hgt * kHB; e += 256) {
+          const int i = e / kHB, q = e - i * kHB;
+          const int64_t R = r0 + i, dq = k0 + q;
+          Vs[e] = (q < w) ? ((R < dq) ? 0.0 : (R == dq ? 1.0 : B[R + dq * d])) : 0.0;
+        }
+        __syncthreads();
+        if (active) {
+          const int rpg = (hgt + Gr - 1) / Gr;
+          const int i0 = g * rpg, i1 = min(hgt, i0 + rpg);
+          for (int i = i0; i < i1; ++i) {
+            const double c = cj[r0 + i];
+            const double* vr = Vs + i * kHB;
+#pragma unroll
+            for (int q = 0; q < kHB; ++q) acc[q] = fma(vr[q], c, acc[q]);
+          }
+        }
+        __syncthreads();
+      }
+      if (active)
+#pragma unroll
+        for (int q = 0; q < kHB; ++q) Gq[(g * nc + jl) * kHB + q] = acc[q];
+      __syncthreads();
+      if (active && g == 0)
+#pragma unroll
+        for (int q = 0; q < kHB; ++q) {
+          double t = 0.0;
+          for (int gg = 0; gg < Gr; ++gg) t += Gq[(gg * nc + jl) * kHB + q];
+          Wc[(cb + jl) * kHB + q] = t;
+        }
+      __syncthreads();
+    }
+    cluster_sync();
+    // ---- Y = T^T (sum over the cluster of W), for every trailing column
+    for (int j = tid; j < ncols; j += 256) {
+      double wv[kHB];
+#pragma unroll
+      for (int q = 0; q < kHB; ++q) wv[q] = 0.0;
+      for (uint32_t c = 0; c < C; ++c) {
+        const uint32_t base = map_shared(Wc + j * kHB, c);
+#pragma unroll
+        for (int q = 0; q < kHB; ++q) wv[q] += ld_cluster_f64(base + 8u * q);
+      }
+#pragma unroll
+      for (int q = 0; q < kHB; ++q) {
+        double y = 0.0;
+#pragma unroll
+        for (int a = 0; a <= q; ++a) y = fma(T[a * kHB + q], wv[a], y);
+        Ys[j * kHB + q] = y;
+      }
+    }
+    __syncthreads();
+    // ---- C <- C - V Y on this CTA's rows
+    for (int cb = 0; cb < ncols; cb += 256) {
+      const int nc = min(256, ncols - cb);
+      const int Gr = max(1, 256 / nc);
+      const int g = tid / nc, jl = tid - g * nc;
+      const bool active = g < Gr;
+      double* cj = B + (int64_t)(j0 + cb + jl) * d;
+      double y[kHB];
+#pragma unroll
+      for (int q = 0; q < kHB; ++q) y[q] = active ? Ys[(cb + jl) * kHB + q] : 0.0;
+      for (int64_t r0 = lo; r0 < rhi; r0 += kHChunk) {
+        const int hgt = (int)min((int64_t)kHChunk, rhi - r0);
+        for (int e = tid; e < hgt * kHB; e += 256) {
+          const int i = e / kHB, q = e - i * kHB;
+          const int64_t R = r0 + i, dq = k0 + q;
+          Vs[e] = (q < w) ? ((R < dq) ? 0.0 : (R == dq ? 1.0 : B[R + dq * d])) : 0.0;
+        }
+        __syncthreads();
+        if (active) {
+          const int rpg = (hgt + Gr - 1) / Gr;
+          const int i0 = g * rpg, i1 = min(hgt, i0 + rpg);
+          for (int i = i0; i < i1; ++i) {
+            double c = cj[r0 + i];
+            const double* vr = Vs + i * kHB;
+#pragma unroll
+            for (int q = 0; q < kHB; ++q) c = fma(-vr[q], y[q], c);
+            cj[r0 + i] = c;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  cluster_sync();                                  // no CTA leaves while others read its shared memory
+}
+
+// R_p, R_p^T and 1/diag(R_p) of the listed problems (all when list is null).
+__global__ void k_b_prepare_R(const BProb* __restrict__ P, const int* __restrict__ list, int count, BPools pl) {
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int p = list ? list[idx] : idx;
     const BProb pr = P[p];
     const int n = (int)pr.n;
-    const double* B = Bpool + pr.boff;
-    double* R = Rpool + pr.roff;
-    double* Rt = Rtpool + pr.roff;
+    const double* B = pl.B + pr.boff;
+    double* R = bR(pl, pr);
+    double* Rt = bRt(pl, pr);
+    double* invd = bvec(pl, pr, V_INVD);
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       const int j = e / n, i = e - j * n;
       const double r = (i <= j) ? B[i + (int64_t)j * pr.d] : 0.0;
       R[i + (int64_t)j * n] = r;
       Rt[j + (int64_t)i * n] = r;
       if (i == j) {
-        invd[pr.voff + i] = 1.0 / r;
-        if (r == 0.0 || !isfinite(r)) atomicOr(&pstatus[p], LS_DEV_RANK);
+        invd[i] = 1.0 / r;
+        if (r == 0.0 || !isfinite(r)) atomicOr(&pl.pstatus[p], LS_DEV_RANK);
       }
     }
   }
@@ -474,20 +710,21 @@ __global__ void k_b_prepare_R(const BProb* __restrict__ P, int np, const double*
 
 // One 1-CTA cluster per problem: x0 = R^{-1} z, normest, condest (the same
 // steps as the single-problem post-factor kernel).
-__global__ void __launch_bounds__(256) k_b_post_factor(const BProb* __restrict__ P, BPools pl) {
-  const int p = blockIdx.x;
+__global__ void __launch_bounds__(256) k_b_post_factor(const BProb* __restrict__ P, const int* __restrict__ list,
+                                                       BPools pl) {
+  const int p = list ? list[blockIdx.x] : blockIdx.x;
   if (pl.pstatus[p] & LS_DEV_RANK) return;
   const BProb pr = P[p];
   const CL cl{0u, 1u};
   const int n = (int)pr.n;
   const double* B = pl.B + pr.boff;
-  const double* R = pl.R + pr.roff;
-  const double* Rt = pl.Rt + pr.roff;
-  const double* invd = pl.inv_diag + pr.voff;
-  double* work = pl.work + pr.voff;
-  double* v = pl.v + pr.voff;
-  double* w = pl.w + pr.voff;
-  double* xi = pl.xi + pr.voff;
+  const double* R = bR(pl, pr);
+  const double* Rt = bRt(pl, pr);
+  const double* invd = bvec(pl, pr, V_INVD);
+  double* work = bvec(pl, pr, V_WORK);
+  double* v = bvec(pl, pr, V_V);
+  double* w = bvec(pl, pr, V_W);
+  double* xi = bvec(pl, pr, V_XI);
   double* slots = pl.slots + (size_t)p * 64;
   cl_load_owned(cl, n, B + (int64_t)n * pr.d, work);
   cl_solve_R(cl, R, n, n, invd, work, pr.x);
@@ -571,27 +808,40 @@ __global__ void __launch_bounds__(256) k_b_post_factor(const BProb* __restrict__
 
 // ---------------------------------------------------------------- iterate
 // Per-problem iteration state set-up: x_prev = x0, state from the estimates.
-__global__ void k_b_iter_init(const BProb* __restrict__ P, int np, BPools pl, double gamma, double rho, double alpha,
-                              double beta) {
-  for (int p = blockIdx.x; p < np; p += gridDim.x) {
+// r_prev is not read before it is written (the first pass has no previous
+// residual), so it needs no clearing.
+__global__ void k_b_iter_init(const BProb* __restrict__ P, const int* __restrict__ list, int count, BPools pl,
+                              double gamma, double rho, double alpha, double beta) {
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int p = list ? list[idx] : idx;
     const BProb pr = P[p];
-    for (int i = threadIdx.x; i < pr.n; i += blockDim.x) pl.x_prev[pr.voff + i] = pr.x[i];
+    const bool rank = (pl.pstatus[p] & LS_DEV_RANK) != 0;
+    double* xp = bvec(pl, pr, V_XPREV);
+    if (!rank)
+      for (int i = threadIdx.x; i < pr.n; i += blockDim.x) xp[i] = pr.x[i];
     if (threadIdx.x == 0) {
       IterState s{};
       s.gamma = gamma; s.rho = rho; s.alpha = alpha; s.beta = beta;
-      s.normest = pl.est[2 * p];
-      s.condest = pl.est[2 * p + 1];
-      if (pl.pstatus[p] & LS_DEV_RANK) { s.done = 1; s.stop_reason = 4; }
+      s.normest = rank ? 0.0 : pl.est[2 * p];
+      s.condest = rank ? 0.0 : pl.est[2 * p + 1];
+      // a rank-deficient problem is reported by the next k_b_step (so that
+      // every completion is recorded by the kernel on the iteration stream)
+      if (rank) s.pad = 1;
+      s.done = 1;
       pl.st[p] = s;
+      __threadfence();
+      *reinterpret_cast<volatile int*>(&pl.st[p].done) = 0;   // published last
     }
   }
 }
 
 static constexpr int kBThreads = 256;
 static constexpr int kBTileCap = 3840;      // doubles per tile buffer (30 KB): 3 CTAs per SM
+static constexpr int kBItemRows = 128;      // rows per pass item (one partial per item)
 
 // Active problems in index order (alist) and the exclusive prefix of their
-// pass tiles (aoff); cnt[0] = active problems, cnt[1] = their tiles.
+// pass items (aoff); cnt[0] = active problems, cnt[1] = their items, cnt[2] =
+// the pass's work counter (items handed out beyond the first gridDim.x).
 __global__ void __launch_bounds__(1024) k_b_compact(const BProb* __restrict__ P, int np,
                                                     const IterState* __restrict__ st, int* __restrict__ alist,
                                                     int64_t* __restrict__ aoff, int64_t* __restrict__ cnt) {
@@ -603,7 +853,7 @@ __global__ void __launch_bounds__(1024) k_b_compact(const BProb* __restrict__ P,
   for (int base = 0; base < np; base += blockDim.x) {
     const int p = base + threadIdx.x;
     const int64_t fa = (p < np && !st[p].done) ? 1 : 0;
-    const int64_t ft = fa ? (int64_t)P[p].tiles : 0;
+    const int64_t ft = fa ? (int64_t)P[p].items : 0;
     int64_t ia = fa, it = ft;                         // inclusive warp scans
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -629,7 +879,7 @@ __global__ void __launch_bounds__(1024) k_b_compact(const BProb* __restrict__ P,
     if (threadIdx.x == 0) { carry_a += wa[(blockDim.x >> 5) - 1]; carry_t += wt[(blockDim.x >> 5) - 1]; }
     __syncthreads();
   }
-  if (threadIdx.x == 0) { cnt[0] = carry_a; cnt[1] = carry_t; }
+  if (threadIdx.x == 0) { cnt[0] = carry_a; cnt[1] = carry_t; cnt[2] = 0; }
 }
 
 __device__ inline void bulk_load(void* smem_dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -640,8 +890,8 @@ __device__ inline void bulk_load(void* smem_dst, const void* src, uint32_t bytes
 }
 
 struct BItem {
-  int64_t v;        // tile index in the active list (-1: none)
-  int p, tile;
+  int64_t v;        // item index in the active list (-1: none)
+  int p, item;
 };
 
 // Issue the copies of one tile of problem pr into buf (warp 0; lane 0 sets
@@ -660,21 +910,23 @@ __device__ inline void b_issue_tile(const BProb& pr, int tile, double* buf, uint
   }
 }
 
-__device__ inline BItem b_locate(const int* __restrict__ alist, const int64_t* __restrict__ aoff, int na,
-                                 const BProb* __restrict__ P, int64_t v, int64_t items) {
+__device__ inline BItem b_locate(const int* __restrict__ alist, const int64_t* __restrict__ aoff, int na, int64_t v,
+                                 int64_t items) {
   BItem it{-1, 0, 0};
   if (v >= items) return it;
   const int i = find_problem(aoff, na, v);
   it.v = v;
   it.p = alist[i];
-  it.tile = (int)(v - aoff[i]);
+  it.item = (int)(v - aoff[i]);
   return it;
 }
 
-// Persistent pass over the tiles of the active problems.
+// Persistent pass over the items (runs of tpi consecutive row tiles) of the
+// active problems.  Column sums of A^T r and the two squared norms are kept
+// in registers across the tiles of an item; one partial per item.
 __global__ void __launch_bounds__(kBThreads, 3) k_b_pass(const BProb* __restrict__ P, const int* __restrict__ alist,
                                                          const int64_t* __restrict__ aoff,
-                                                         const int64_t* __restrict__ cnt, BPools pl, int max_n,
+                                                         int64_t* __restrict__ cnt, BPools pl, int max_n,
                                                          unsigned int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* buf0 = reinterpret_cast<double*>(smem_raw);
@@ -685,6 +937,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_b_pass(const BProb* __restrict
   double* q2 = q1 + kBThreads;                       // 256: r_j - r_prev_j
   double* gs = q2 + kBThreads;                       // 256: phase-2 group sums
   uint64_t* bar = reinterpret_cast<uint64_t*>(gs + kBThreads);
+  __shared__ int64_t s_next;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int na = (int)cnt[0];
   const int64_t items = cnt[1];
@@ -695,114 +948,150 @@ __global__ void __launch_bounds__(kBThreads, 3) k_b_pass(const BProb* __restrict
     fence_mbar_init();
   }
   __syncthreads();
-  BItem cur = b_locate(alist, aoff, na, P, blockIdx.x, items);
-  if (warp == 0) b_issue_tile(P[cur.p], cur.tile, buf0, &bar[0], lane);
-  int k = 0;
+  // items are handed out dynamically (CTAs that start late, e.g. behind other
+  // kernels' CTAs, take fewer); which CTA computes an item does not change it
+  BItem cur = b_locate(alist, aoff, na, blockIdx.x, items);
+  int k = 0;                                          // tiles consumed by this CTA
+  if (warp == 0) {
+    const BProb& pr0 = P[cur.p];
+    b_issue_tile(pr0, cur.item * pr0.tpi, buf0, &bar[0], lane);
+  }
   while (cur.v >= 0) {
-    const BItem nxt = b_locate(alist, aoff, na, P, cur.v + gridDim.x, items);
-    double* tl = buf0 + (size_t)(k & 1) * kBTileCap;
-    // the other buffer was last read by the previous tile, finished at the
-    // closing __syncthreads
-    if (warp == 0 && nxt.v >= 0)
-      b_issue_tile(P[nxt.p], nxt.tile, buf0 + (size_t)((k + 1) & 1) * kBTileCap, &bar[(k + 1) & 1], lane);
+    if (tid == 0)
+      s_next = (int64_t)gridDim.x + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(cnt + 2), 1ull);
+    __syncthreads();
+    const BItem nxt = b_locate(alist, aoff, na, s_next, items);
     const BProb pr = P[cur.p];
     const int n = (int)pr.n, TR = pr.tr, ss = pr.ss, S = pr.S;
-    const int64_t row0 = (int64_t)cur.tile * TR;
-    const int rows = (int)min((int64_t)TR, pr.m - row0);
+    const int t0 = cur.item * pr.tpi, t1 = min(pr.tiles, t0 + pr.tpi);
     for (int i = tid; i < n; i += kBThreads) xs[i] = pr.x[i];
-    const bool ok = mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1, gtimer() + LS_WAIT_NS);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(status, LS_DEV_TIMEOUT);
-      if (tid == 0 && nxt.v >= 0) mbar_wait_bounded(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1, gtimer() + LS_WAIT_NS);
-      return;
-    }
-    // phase 1: partial row dots, thread = (row r, column chunk s)
     const int clen = (n + S - 1) / S;
-    if (tid < S * TR) {
-      const int r = tid % TR, sidx = tid / TR;
-      if (r < rows) {
-        const int c0 = sidx * clen, c1 = min(n, c0 + clen);
-        const double* a = tl + (size_t)r * ss;
-        // four interleaved accumulators: a dot of rounding error ~ (len/4 + 2) u
-        // instead of len u (the stopping rule compares r_i - r_{i-1} with u)
-        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
-        int c = c0;
-        for (; c + 3 < c1; c += 4) {
-          d0 = fma(a[c], xs[c], d0);
-          d1 = fma(a[c + 1], xs[c + 1], d1);
-          d2 = fma(a[c + 2], xs[c + 2], d2);
-          d3 = fma(a[c + 3], xs[c + 3], d3);
+    const int G = (n < kBThreads) ? kBThreads / n : 1;
+    const int g = (n < kBThreads) ? tid / n : 0, cg = (n < kBThreads) ? tid - g * n : tid;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};            // column sums (n >= 256: columns tid + 256 u)
+    double nv = 0.0;                                  // warps 0 / 1: squared norms
+    for (int t = t0; t < t1; ++t, ++k) {
+      // prefetch the next tile of this item, else the first tile of the next item
+      if (warp == 0) {
+        double* nb = buf0 + (size_t)((k + 1) & 1) * kBTileCap;
+        if (t + 1 < t1) b_issue_tile(pr, t + 1, nb, &bar[(k + 1) & 1], lane);
+        else if (nxt.v >= 0) {
+          const BProb& pn = P[nxt.p];
+          b_issue_tile(pn, nxt.item * pn.tpi, nb, &bar[(k + 1) & 1], lane);
         }
-        if (c < c1) d0 = fma(a[c], xs[c], d0);
-        if (c + 1 < c1) d1 = fma(a[c + 1], xs[c + 1], d1);
-        if (c + 2 < c1) d2 = fma(a[c + 2], xs[c + 2], d2);
-        part1[tid] = (d0 + d1) + (d2 + d3);
       }
-    }
-    __syncthreads();
-    double* rp = pl.r_prev + pr.moff + row0;
-    if (tid < TR) {
-      double v1 = 0.0, v2 = 0.0;
-      if (tid < rows) {
-        double dot = part1[tid];
-        for (int sidx = 1; sidx < S; ++sidx) dot += part1[sidx * TR + tid];
-        const double rj = __ldg(pr.b + row0 + tid) - dot;
-        const double dl = rj - rp[tid];
-        rp[tid] = rj;
-        rt[tid] = rj;
-        v1 = rj;
-        v2 = dl;
+      const bool more = (t + 1 < t1) || (nxt.v >= 0);
+      const double* tl = buf0 + (size_t)(k & 1) * kBTileCap;
+      const int64_t row0 = (int64_t)t * TR;
+      const int rows = (int)min((int64_t)TR, pr.m - row0);
+      const bool ok = mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1, gtimer() + LS_WAIT_NS);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(status, LS_DEV_TIMEOUT);
+        if (tid == 0 && more) mbar_wait_bounded(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1, gtimer() + LS_WAIT_NS);
+        return;
       }
-      q1[tid] = v1;
-      q2[tid] = v2;
+      // phase 1: partial row dots, thread = (row r, column chunk s)
+      if (tid < S * TR) {
+        const int r = tid % TR, sidx = tid / TR;
+        if (r < rows) {
+          const int c0 = sidx * clen, c1 = min(n, c0 + clen);
+          const double* a = tl + (size_t)r * ss;
+          // four interleaved accumulators: a dot of rounding error ~ (len/4 + 2) u
+          // instead of len u (the stopping rule compares r_i - r_{i-1} with u)
+          double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+          int c = c0;
+          for (; c + 3 < c1; c += 4) {
+            d0 = fma(a[c], xs[c], d0);
+            d1 = fma(a[c + 1], xs[c + 1], d1);
+            d2 = fma(a[c + 2], xs[c + 2], d2);
+            d3 = fma(a[c + 3], xs[c + 3], d3);
+          }
+          if (c < c1) d0 = fma(a[c], xs[c], d0);
+          if (c + 1 < c1) d1 = fma(a[c + 1], xs[c + 1], d1);
+          if (c + 2 < c1) d2 = fma(a[c + 2], xs[c + 2], d2);
+          part1[tid] = (d0 + d1) + (d2 + d3);
+        }
+      }
+      __syncthreads();
+      double* rp = pl.r_prev + pr.rpoff + row0;
+      if (tid < TR) {
+        double v1 = 0.0, v2 = 0.0;
+        if (tid < rows) {
+          double dot = part1[tid];
+          for (int sidx = 1; sidx < S; ++sidx) dot += part1[sidx * TR + tid];
+          const double rj = __ldg(pr.b + row0 + tid) - dot;
+          const double dl = rj - rp[tid];
+          rp[tid] = rj;
+          rt[tid] = rj;
+          v1 = rj;
+          v2 = dl;
+        }
+        q1[tid] = v1;
+        q2[tid] = v2;
+      }
+      __syncthreads();
+      // phase 2: c_k += sum_r A_rk r_r over the tile
+      if (n >= kBThreads) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = tid + u * kBThreads;
+          if (c < n)
+            for (int r = 0; r < rows; ++r) acc[u] = fma(tl[(size_t)r * ss + c], rt[r], acc[u]);
+        }
+      } else if (g < G) {
+        for (int r = g; r < rows; r += G) acc[0] = fma(tl[(size_t)r * ss + cg], rt[r], acc[0]);
+      }
+      if (warp < 2) {
+        const double* q = warp ? q2 : q1;
+        for (int r = lane; r < TR; r += 32) nv = fma(q[r], q[r], nv);
+      }
+      __syncthreads();                                // the buffer and rt are reused next
     }
-    __syncthreads();
-    // phase 2: c_k = sum_r A_rk r_r over the tile
-    double* out = pl.part + pr.poff + (int64_t)cur.tile * (n + 2);
+    // the item's partial (c, ||r||^2, ||r - r_prev||^2)
+    double* out = pl.part + pr.poff + (int64_t)cur.item * (n + 2);
     if (n >= kBThreads) {
-      for (int c = tid; c < n; c += kBThreads) {
-        double acc = 0.0;
-        for (int r = 0; r < rows; ++r) acc = fma(tl[(size_t)r * ss + c], rt[r], acc);
-        out[c] = acc;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = tid + u * kBThreads;
+        if (c < n) out[c] = acc[u];
       }
     } else {
-      const int G = kBThreads / n;
-      const int g = tid / n, c = tid - g * n;
-      if (g < G) {
-        double acc = 0.0;
-        for (int r = g; r < rows; r += G) acc = fma(tl[(size_t)r * ss + c], rt[r], acc);
-        gs[g * n + c] = acc;
-      }
-    }
-    // the two squared norms of this tile (warps 0 and 1, fixed order)
-    if (warp < 2) {
-      const double* q = warp ? q2 : q1;
-      double v = 0.0;
-      for (int r = lane; r < TR; r += 32) v = fma(q[r], q[r], v);
-      v = warp_sum(v);
-      if (lane == 0) out[n + warp] = v;
-    }
-    if (n < kBThreads) {
+      if (g < G) gs[g * n + cg] = acc[0];
       __syncthreads();
-      const int G = kBThreads / n;
       for (int c = tid; c < n; c += kBThreads) {
         double t = 0.0;
-        for (int g = 0; g < G; ++g) t += gs[g * n + c];
+        for (int gg = 0; gg < G; ++gg) t += gs[gg * n + c];
         out[c] = t;
       }
     }
-    __syncthreads();
+    if (warp < 2) {
+      nv = warp_sum(nv);
+      if (lane == 0) out[n + warp] = nv;
+    }
+    __syncthreads();                                  // gs and xs are reused by the next item
     cur = nxt;
-    ++k;
   }
 }
 
 // One 1-CTA cluster per problem: sum partials (item order), stopping rule,
 // two substitutions, update.
-__global__ void __launch_bounds__(256) k_b_step(const BProb* __restrict__ P, BPools pl, int use_stop, int extra) {
-  const int p = blockIdx.x;
+__global__ void __launch_bounds__(256) k_b_step(const BProb* __restrict__ P, const int* __restrict__ alist,
+                                                const int64_t* __restrict__ cnt, BPools pl, int use_stop, int extra,
+                                                int q) {
+  // only the problems the pass just served (the list k_b_compact made)
+  if ((int64_t)blockIdx.x >= cnt[0]) return;
+  const int p = alist[blockIdx.x];
   IterState S = pl.st[p];
   if (S.done) return;
+  if (S.pad) {                      // rank deficient at factorization: report it now
+    if (threadIdx.x == 0) {
+      IterState& st = pl.st[p];
+      st.done = 1;
+      st.stop_reason = 4;
+      b_record_done(pl, p, st);
+    }
+    return;
+  }
   const BProb pr = P[p];
   const CL cl{0u, 1u};
   const int n = (int)pr.n;
@@ -810,7 +1099,7 @@ __global__ void __launch_bounds__(256) k_b_step(const BProb* __restrict__ P, BPo
   __shared__ double s_norm[2];
   if (threadIdx.x < 2) {
     double s = 0.0;
-    for (int t = 0; t < pr.tiles; ++t) s += part[(int64_t)t * (n + 2) + n + threadIdx.x];
+    for (int t = 0; t < pr.items; ++t) s += part[(int64_t)t * (n + 2) + n + threadIdx.x];
     s_norm[threadIdx.x] = s;
   }
   __syncthreads();
@@ -830,26 +1119,28 @@ __global__ void __launch_bounds__(256) k_b_step(const BProb* __restrict__ P, BPo
   }
   if (done) {
     if (threadIdx.x == 0) {
-      pl.st[p].done = 1; pl.st[p].fired = 1; pl.st[p].stop_reason = 0;
-      pl.st[p].rnorm = rnorm; pl.st[p].dnorm = dnorm;
+      IterState& st = pl.st[p];
+      st.done = 1; st.fired = 1; st.stop_reason = 0;
+      st.rnorm = rnorm; st.dnorm = dnorm;
+      b_record_done(pl, p, st);
     }
     return;
   }
-  double* work = pl.work + pr.voff;
+  double* work = bvec(pl, pr, V_WORK);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double s = 0.0;
-    for (int t = 0; t < pr.tiles; ++t) s += part[(int64_t)t * (n + 2) + i];
+    for (int t = 0; t < pr.items; ++t) s += part[(int64_t)t * (n + 2) + i];
     __stcg(work + i, s);
   }
   __syncthreads();
-  const double* invd = pl.inv_diag + pr.voff;
-  double* y = pl.y + pr.voff;
-  double* dv = pl.dvec + pr.voff;
-  cl_solve_RT(cl, pl.Rt + pr.roff, n, invd, work, y);
+  const double* invd = bvec(pl, pr, V_INVD);
+  double* y = bvec(pl, pr, V_Y);
+  double* dv = bvec(pl, pr, V_D);
+  cl_solve_RT(cl, bRt(pl, pr), n, invd, work, y);
   cl_load_owned(cl, n, y, work);
-  cl_solve_R(cl, pl.R + pr.roff, n, n, invd, work, dv);
+  cl_solve_R(cl, bR(pl, pr), n, n, invd, work, dv);
   double xs = 0.0, bad = 0.0;
-  double* xp = pl.x_prev + pr.voff;
+  double* xp = bvec(pl, pr, V_XPREV);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double xi = pr.x[i], xpi = xp[i], di = __ldcg(dv + i);
     const double xn = xi + S.alpha * di + S.beta * (xi - xpi);
@@ -869,7 +1160,12 @@ __global__ void __launch_bounds__(256) k_b_step(const BProb* __restrict__ P, BPo
     st.xnorm = sqrt(xs);
     st.rnorm = rnorm;
     st.dnorm = dnorm;
-    if (bad != 0.0) { st.nonfinite = 1; st.done = 1; st.stop_reason = 3; }
+    if (bad != 0.0) {
+      st.nonfinite = 1; st.done = 1; st.stop_reason = 3;
+    } else if (st.iter >= q) {
+      st.done = 1; st.stop_reason = use_stop ? 1 : 2;
+    }
+    if (st.done) b_record_done(pl, p, st);
   }
 }
 
@@ -891,6 +1187,7 @@ void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl) {
   pl.np = np;
   pl.mtotal = pl.dtotal = pl.btotal = pl.rtotal = pl.vtotal = pl.ttotal = pl.ptotal = pl.wtotal = 0;
   pl.max_d = 0;
+  pl.max_m = 0;
   pl.max_fill = 0.0;
   pl.max_n = 0;
   pl.max_tile_doubles = 0;
@@ -899,14 +1196,18 @@ void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl) {
     BProb b{};
     b.A = q.A; b.b = q.b; b.x = q.x; b.m = q.m; b.n = q.n; b.lda = q.lda; b.d = q.d; b.seed = q.seed;
     b.moff = pl.mtotal; b.doff = pl.dtotal; b.boff = pl.btotal; b.roff = pl.rtotal; b.voff = pl.vtotal;
+    b.rpoff = pl.mtotal;
     b.toff = pl.wtotal; b.poff = pl.ptotal;
     pass_tile(q.n, q.lda, b);
     b.gw = (q.n + 1 > 16) ? 32 : (q.n + 1 > 8) ? 16 : (q.n + 1 > 4) ? 8 : 4;
     b.tiles = (int)((q.m + b.tr - 1) / b.tr);
-    pl.mtotal += q.m; pl.dtotal += q.d; pl.btotal += q.d * (q.n + 1); pl.rtotal += q.n * q.n;
-    pl.vtotal += q.n; pl.ttotal += b.tiles; pl.ptotal += (int64_t)b.tiles * (q.n + 2);
+    b.tpi = std::max(1, (kBItemRows + b.tr - 1) / b.tr);
+    b.items = (b.tiles + b.tpi - 1) / b.tpi;
+    pl.mtotal += q.m; pl.dtotal += q.d; pl.btotal += q.d * (q.n + 1); pl.rtotal += 2 * q.n * q.n;
+    pl.vtotal += V_COUNT * q.n; pl.ttotal += b.items; pl.ptotal += (int64_t)b.items * (q.n + 2);
     pl.wtotal += (q.d + (32 / b.gw) - 1) / (32 / b.gw);
     pl.max_d = std::max<int64_t>(pl.max_d, q.d);
+    pl.max_m = std::max<int64_t>(pl.max_m, q.m);
     pl.max_fill = std::max<double>(pl.max_fill, (double)q.m / (double)q.d);
     pl.max_n = std::max<int>(pl.max_n, (int)q.n);
 
@@ -948,6 +1249,7 @@ cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* dwoffs,
 }
 
 bool b_csr_fits(const BatchPlan& pl) { return pl.max_d <= kCsrMaxD; }
+int64_t b_csr_max_d() { return kCsrMaxD; }
 
 cudaError_t launch_b_csr(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, int zeta, const int32_t* rows,
                          const uint32_t* signs, int64_t* row_ptr, uint32_t* ent, uint32_t* scratch) {
@@ -960,39 +1262,127 @@ cudaError_t launch_b_csr(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, int 
   return cudaGetLastError();
 }
 
-void batch_order(const BProb* P, int np, int* order) {
-  for (int p = 0; p < np; ++p) order[p] = p;
-  std::stable_sort(order, order + np, [&](int a, int b) {
+// Factorization plan: problems with n >= kCQMinN (and n <= kCQMaxN) get a
+// thread-block cluster each, the rest one CTA each in order of decreasing
+// work (d n^2).  order[0 .. nsmall) = the one-CTA problems, order[nsmall ..
+// np) = the cluster problems.  Returns nsmall.
+int batch_order(const BProb* P, int np, int* order, bool clusters) {
+  int ns = 0;
+  for (int p = 0; p < np; ++p)
+    if (!(clusters && P[p].n >= kCQMinN && P[p].n <= kCQMaxN)) order[ns++] = p;
+  int nb = ns;
+  for (int p = 0; p < np; ++p)
+    if (clusters && P[p].n >= kCQMinN && P[p].n <= kCQMaxN) order[nb++] = p;
+  std::stable_sort(order, order + ns, [&](int a, int b) {
     return (double)P[a].d * P[a].n * P[a].n > (double)P[b].d * P[b].n * P[b].n;
   });
+  return ns;
 }
 
-cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const int* dorder, const BatchPlan& pl,
-                            const BPools& pools) {
-  k_b_householder<<<pl.np, 256, 0, ctx->stream>>>(dP, dorder, pools.B, pools.pstatus);
+size_t b_qr_cluster_smem() { return sizeof(double) * (2 * (size_t)kCQW + 256 * kHB + kHChunk * kHB); }
+int b_qr_cluster_max_n() { return kCQMaxN; }
+
+// CTAs per cluster for k_b_qr_cluster on this device: 16 where a 16-CTA
+// cluster of this kernel fits, else 8, else 0 (not usable).
+int b_qr_cluster_size(ls_ctx* ctx) {
+  const size_t smem = b_qr_cluster_smem();
+  if (cudaFuncSetAttribute(k_b_qr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  cudaFuncSetAttribute(k_b_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_b_qr_cluster, &cfg) == cudaSuccess && nclusters > 0) return c;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+// Cluster QR of the `count` problems listed in dlist (device), csize CTAs each.
+cudaError_t launch_b_qr_cluster(ls_ctx* ctx, const BProb* dP, const int* dlist, int count, int csize,
+                                const BPools& pools) {
+  if (count == 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * csize));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = b_qr_cluster_smem();
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const BProb* a0 = dP;
+  const int* a1 = dlist;
+  double* a2 = pools.B;
+  unsigned int* a3 = pools.pstatus;
+  void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3};
   ++ctx->launches;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_b_prepare_R<<<std::min(pl.np, ctx->num_sms * 8), 256, 0, ctx->stream>>>(dP, pl.np, pools.B, pools.R, pools.Rt,
-                                                                          pools.inv_diag, pools.pstatus);
+  return cudaLaunchKernelExC(&cfg, (const void*)k_b_qr_cluster, args);
+}
+
+// Householder QR of `count` problems: the first `nsmall` entries of dorder
+// one CTA each; `nbig` problems listed in dbig (may be null) one cluster
+// each.  Then R, R^T, 1/diag(R), x0 and the estimates of all `count` listed
+// problems (list; null = 0 .. count-1).
+cudaError_t launch_b_factor2(ls_ctx* ctx, const BProb* dP, const int* dorder, int nsmall, const int* dbig, int nbig,
+                             int csize, int count, const int* list, const BPools& pools) {
+  cudaError_t e;
+  if (nbig > 0 && (e = launch_b_qr_cluster(ctx, dP, dbig, nbig, csize, pools)) != cudaSuccess) return e;
+  if (nsmall > 0) {
+    k_b_householder<<<nsmall, 256, 0, ctx->stream>>>(dP, dorder, pools.B, pools.pstatus);
+    ++ctx->launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_b_prepare_R<<<std::min(count, ctx->num_sms * 8), 256, 0, ctx->stream>>>(dP, list, count, pools);
   ++ctx->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   BPools pp = pools;
   const BProb* dPP = dP;
-  void* args[] = {(void*)&dPP, &pp};
-  return launch_cluster_grid(ctx, (const void*)k_b_post_factor, args, pl.np);
+  const int* lp = list;
+  void* args[] = {(void*)&dPP, (void*)&lp, &pp};
+  return launch_cluster_grid(ctx, (const void*)k_b_post_factor, args, count);
 }
 
-cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, double gamma,
-                               double rho, double alpha, double beta) {
-  k_b_iter_init<<<std::min(pl.np, ctx->num_sms * 8), 128, 0, ctx->stream>>>(dP, pl.np, pools, gamma, rho, alpha, beta);
+cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const int* dorder, int count, const int* list,
+                            const BPools& pools) {
+  k_b_householder<<<count, 256, 0, ctx->stream>>>(dP, dorder, pools.B, pools.pstatus);
+  ++ctx->launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_b_prepare_R<<<std::min(count, ctx->num_sms * 8), 256, 0, ctx->stream>>>(dP, list, count, pools);
+  ++ctx->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  BPools pp = pools;
+  const BProb* dPP = dP;
+  const int* lp = list;
+  void* args[] = {(void*)&dPP, (void*)&lp, &pp};
+  return launch_cluster_grid(ctx, (const void*)k_b_post_factor, args, count);
+}
+
+cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, int count, const int* list, const BPools& pools,
+                               double gamma, double rho, double alpha, double beta) {
+  k_b_iter_init<<<std::min(count, ctx->num_sms * 8), 128, 0, ctx->stream>>>(dP, list, count, pools, gamma, rho,
+                                                                           alpha, beta);
   ++ctx->launches;
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int* alist,
-                             int64_t* aoff, int64_t* cnt) {
-  k_b_compact<<<1, 1024, 0, ctx->stream>>>(dP, pl.np, pools.st, alist, aoff, cnt);
+cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, int np, const BPools& pools, int* alist, int64_t* aoff,
+                             int64_t* cnt) {
+  k_b_compact<<<1, 1024, 0, ctx->stream>>>(dP, np, pools.st, alist, aoff, cnt);
   ++ctx->launches;
   return cudaGetLastError();
 }
@@ -1001,27 +1391,36 @@ size_t b_pass_smem(int max_n) {
   return sizeof(double) * (2 * (size_t)kBTileCap + (size_t)((max_n + 1) & ~1) + 5 * kBThreads) + 2 * sizeof(uint64_t);
 }
 
-cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* aoff, const int64_t* cnt,
-                          const BatchPlan& pl, const BPools& pools) {
-  const size_t smem = b_pass_smem(pl.max_n);
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_b_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return e;
+// Grid of the persistent pass for problems of up to max_n columns (also
+// sets the kernel's shared-memory limit; call before capturing a launch).
+int b_pass_grid(ls_ctx* ctx, int max_n) {
+  const size_t smem = b_pass_smem(max_n);
+  if (cudaFuncSetAttribute(k_b_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_pass, kBThreads, smem);
-  const int64_t grid = std::min<int64_t>(pl.ttotal, (int64_t)ctx->num_sms * std::max(1, per_sm));
-  k_b_pass<<<(unsigned)grid, kBThreads, smem, ctx->stream>>>(dP, alist, aoff, cnt, pools, pl.max_n, ctx->d_status);
+  return ctx->num_sms * std::max(1, per_sm);
+}
+
+cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* aoff, int64_t* cnt,
+                          int max_n, int64_t max_items, const BPools& pools) {
+  const size_t smem = b_pass_smem(max_n);
+  const int g = b_pass_grid(ctx, max_n);
+  if (g == 0) return cudaErrorInvalidValue;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(max_items, (int64_t)g));
+  k_b_pass<<<(unsigned)grid, kBThreads, smem, ctx->stream>>>(dP, alist, aoff, cnt, pools, max_n, ctx->d_status);
   ++ctx->launches;
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_step(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int use_stop,
-                          int extra) {
+cudaError_t launch_b_step(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* cnt, int np,
+                          const BPools& pools, int use_stop, int extra, int q) {
   BPools pp = pools;
   const BProb* dPP = dP;
-  int us = use_stop, ex = extra;
-  void* args[] = {(void*)&dPP, &pp, &us, &ex};
-  return launch_cluster_grid(ctx, (const void*)k_b_step, args, pl.np);
+  const int* al = alist;
+  const int64_t* cn = cnt;
+  int us = use_stop, ex = extra, qq = q;
+  void* args[] = {(void*)&dPP, (void*)&al, (void*)&cn, &pp, &us, &ex, &qq};
+  return launch_cluster_grid(ctx, (const void*)k_b_step, args, np);
 }
 
 }  // namespace lsk

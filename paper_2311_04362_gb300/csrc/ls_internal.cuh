@@ -308,7 +308,7 @@ struct IterState {
   int stop_reason;   // 0 rule held, 1 q reached, 3 non-finite
   int nonfinite;
   int have_prev;     // r_prev holds r(x_{i-1})
-  int pad;
+  int pad;           // batched path: 1 = rank deficient, to be reported
   double xnorm;      // ||x_i||
   double rnorm;      // ||r(x_i)||
   double dnorm;      // ||r(x_i) - r(x_{i-1})||
@@ -346,20 +346,53 @@ struct StepArgs {
 cudaError_t launch_iter_step(ls_ctx* ctx, const StepArgs& a);
 
 // batched path (batched.cu)
-struct BProb;
+// One problem of a batched solve or one server slot: caller's arrays, sizes,
+// offsets of its parts in the pools, and its pass tile geometry.
+struct BProb {
+  const double* A; const double* b; double* x;
+  int64_t m, n, lda, d;
+  uint64_t seed;
+  int64_t moff;      // sum of m over earlier problems (flattened columns of S)
+  int64_t doff;      // sum of d (buckets)
+  int64_t boff;      // sum of d (n + 1) (B pool)
+  int64_t roff;      // R at roff, R^T at roff + n^2 (R pool)
+  int64_t voff;      // 8 n-vectors at voff (V pool): 1/diag R, x_prev, y, d, work, v, w, xi
+  int64_t rpoff;     // r_prev (m doubles) in the r_prev pool
+  int64_t toff;      // sum of gather warps (k_b_gather)
+  int64_t poff;      // sum of tiles (n + 2) (partials)
+  int tr;            // rows per pass tile
+  int tiles;         // pass tiles
+  int ss;            // shared-memory row stride of a tile (doubles, = 2 mod 4)
+  int S;             // column chunks per row in the row-dot phase (S * tr <= 256)
+  int rowcopy;       // 1: one bulk copy per row (lda != ss), 0: one per tile
+  int gw;            // gather lanes per bucket (32, 16, 8 or 4)
+  int tpi;           // pass tiles per item (one partial per item)
+  int items;         // pass items
+};
+// Completion record of a problem (server mode).
+struct BDone {
+  int slot, iters, stop_reason, pad;
+  double res_norm, step_norm, normest, condest;
+};
 struct BPools {
-  double* B; double* R; double* Rt; double* inv_diag;
-  double* x_prev; double* y; double* dvec; double* work; double* v; double* w; double* xi;
-  double* slots; double* est; double* part; double* r_prev;
+  double* B;        // sketches [S A, S b] at boff
+  double* R;        // R at roff, R^T at roff + n^2
+  double* V;        // 8 n-vectors at voff
+  double* part;     // pass partials at poff
+  double* r_prev;   // previous residuals at rpoff
+  double* slots;    // 64 per problem (cluster reductions)
+  double* est;      // normest, condest per problem
   IterState* st;
   unsigned int* pstatus;
+  BDone* done_rec;            // completion queue (null: not recorded)
+  unsigned int* done_count;
 };
 struct BatchPlan {
   int np;
   int64_t mtotal, dtotal, btotal, rtotal, vtotal, ttotal, ptotal;
   int64_t wtotal;                // gather warps
   int max_n, max_tile_doubles;   // max_tile_doubles: unused
-  int64_t max_d;
+  int64_t max_d, max_m;
   double max_fill;               // largest m / d (mean bucket size / zeta)
 };
 bool b_csr_fits(const BatchPlan& pl);
@@ -374,17 +407,22 @@ cudaError_t launch_b_sketch_indices(ls_ctx* ctx, const BProb* dP, const int64_t*
                                     int zeta, int32_t* rows, uint32_t* signs);
 cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* dwoffs, const BatchPlan& pl,
                             const int64_t* row_ptr, const uint32_t* ent, double scale, double* Bpool);
-void batch_order(const BProb* P, int np, int* order);
-cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const int* dorder, const BatchPlan& pl,
+int batch_order(const BProb* P, int np, int* order, bool clusters);
+cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const int* dorder, int count, const int* list,
                             const BPools& pools);
-cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools,
+int b_qr_cluster_size(ls_ctx* ctx);
+int b_qr_cluster_max_n();
+cudaError_t launch_b_factor2(ls_ctx* ctx, const BProb* dP, const int* dorder, int nsmall, const int* dbig, int nbig,
+                             int csize, int count, const int* list, const BPools& pools);
+cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, int count, const int* list, const BPools& pools,
                                double gamma, double rho, double alpha, double beta);
-cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int* alist,
-                             int64_t* aoff, int64_t* cnt);
-cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* aoff, const int64_t* cnt,
-                          const BatchPlan& pl, const BPools& pools);
-cudaError_t launch_b_step(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, const BPools& pools, int use_stop,
-                          int extra);
+cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, int np, const BPools& pools, int* alist, int64_t* aoff,
+                             int64_t* cnt);
+int b_pass_grid(ls_ctx* ctx, int max_n);
+cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* aoff, int64_t* cnt,
+                          int max_n, int64_t max_items, const BPools& pools);
+cudaError_t launch_b_step(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* cnt, int np,
+                          const BPools& pools, int use_stop, int extra, int q);
 cudaError_t launch_correct(ls_ctx* ctx, const StepArgs& a);
 
 }  // namespace lsk

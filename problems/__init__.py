@@ -143,3 +143,18 @@ def make_batch_torch(shapes, device="cuda", lda_even=True):
                           m=s["m"], n=n, lda=A.stride(0), d=s["d"],
                           kappa=s["kappa"], resnorm=s["resnorm"], seed=s["index"]))
     return probs
+
+
+# Serving stream (requests drawn from a pool of such problems): n log-uniform
+# in [20, 500], then m log-uniform in [max(1000, 20 n), 5e5], kappa
+# log-uniform in [1e2, 1e10], ||r|| log-uniform in [1e-8, 1e-2], d = 20 n,
+# zeta = 8; Poisson arrivals at each rate of the sweep.
+SERVE = dict(count=96, m_lo=1000, m_hi=500_000, n_lo=20, n_hi=500, kappa_lo=1e2, kappa_hi=1e10,
+             res_lo=1e-8, res_hi=1e-2, d_over_n=20, zeta=8, q=100, seed=5,
+             rates=(50, 200, 500, 1000, 2000, 5000), requests_per_rate=400, budget_bytes=150 * 10**9)
+
+
+def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson stream of the given rate."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, int(rate), 0xA77]))
+    return np.cumsum(rng.exponential(1.0 / rate, count))
