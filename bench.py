@@ -196,6 +196,7 @@ def main():
     ap.add_argument("--m", type=int, default=200_000, help="rows for --case pass")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-problems timing")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) sweep")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -324,6 +325,10 @@ def main():
     if not args.no_serving:
         serving = serving_case(ctx, args)
 
+    mixed = None
+    if not args.no_mixed:
+        mixed = mixed_case(ctx, stream, args, pg, world)
+
     fe_qr = None
     if args.check_qr and rank == 0:
         import oracle
@@ -358,6 +363,7 @@ def main():
             "variants_app_b": variants,
             "batched": batched,
             "serving": serving,
+            "mixed_precision": mixed,
             "phase_ms": {"sketch": statistics.mean(i.ms_sketch for _, i in infos),
                          "factor": statistics.mean(i.ms_factor for _, i in infos),
                          "iterate": statistics.mean(i.ms_iterate for _, i in infos)},
@@ -508,6 +514,75 @@ def serving_case(ctx, args):
         srv.close()
     del pool, xbuf
     torch.cuda.empty_cache()
+    return out
+
+
+def mixed_case(ctx, stream, args, pg, world):
+    """FP32 sketch and QR (ls_solve_batched_mixed) against all-FP64 on the
+    mixed-precision problem (problems.MIXED): solves/s, iterations, forward
+    error against a Householder-QR solve (geqrf through torch), and the error
+    of each FP32 stage against the FP64 one (relative Frobenius norms)."""
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    import problems
+
+    cfg = problems.MIXED
+    m, n, d = cfg["m"], cfg["n"], cfg["d"]
+    P = problems.make_problem_torch(m, n, cfg["kappa"], cfg["resnorm"], cfg["seed"] + 7, device="cuda")
+    xt = P["x"]
+    Q, R = torch.linalg.qr(P["A"])
+    xq = torch.linalg.solve_triangular(R, (Q.T @ P["b"])[:, None], upper=True)[:, 0]
+    fe_qr = float(torch.linalg.norm(xq - xt) / torch.linalg.norm(xt))
+    del Q, R
+    out = {"workload": "m=1,000,000, n=200, kappa=1e4, ||r||=1e-3, d=4000, zeta=8, seed 0, q <= 100",
+           "fe_qr": fe_qr}
+    stages = {}
+    steps = max(1, args.steps)
+    for name, mixed in (("fp64", False), ("mixed", True)):
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        Bo = torch.empty(d * (n + 1), dtype=torch.float64, device="cuda")
+        Ro = torch.empty(n * n, dtype=torch.float64, device="cuda")
+        prob = dict(A=P["A"], b=P["b"], x=x, m=m, n=n, lda=n, d=d, seed=cfg["seed"], B_out=Bo, R_out=Ro)
+        ctx.ls_solve_batched([prob], cfg["zeta"], cfg["q"], mixed=mixed)       # warm, and the stage outputs
+        stages[name] = (Bo, Ro)
+        run = dict(prob, B_out=None, R_out=None)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            inf = ctx.ls_solve_batched([run], cfg["zeta"], cfg["q"], mixed=mixed)[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+        fe = float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
+        out[name] = {"value": job_throughput(world, steps, ms), "unit": UNIT, "iters": inf.iters,
+                     "stop_reason": inf.stop_reason, "fe": fe, "fe_over_qr": fe / fe_qr,
+                     "phase_ms": {"sketch": inf.ms_sketch, "factor": inf.ms_factor, "iterate": inf.ms_iterate}}
+    # the single-problem FP64 path (multi-CTA QR, TMA-fed pass) on the same problem
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.ls_solve(P["A"], P["b"], m, n, n, d, cfg["zeta"], cfg["q"], cfg["seed"], x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        st, inf = ctx.ls_solve(P["A"], P["b"], m, n, n, d, cfg["zeta"], cfg["q"], cfg["seed"], x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+    fe = float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt))
+    out["fp64_single_path"] = {"value": job_throughput(world, steps, ms), "unit": UNIT, "iters": inf.iters,
+                               "fe": fe, "fe_over_qr": fe / fe_qr,
+                               "phase_ms": {"sketch": inf.ms_sketch, "factor": inf.ms_factor,
+                                            "iterate": inf.ms_iterate}}
+    B64, R64 = stages["fp64"]
+    B32, R32 = stages["mixed"]
+    R64m, R32m = R64.view(n, n), R32.view(n, n)          # column-major n x n: rows of the view are columns
+    sgn = torch.sign(torch.diagonal(R64m)) * torch.sign(torch.diagonal(R32m))
+    out["stage_error"] = {
+        "sketch_rel_fro": float(torch.linalg.norm(B32 - B64) / torch.linalg.norm(B64)),
+        "R_rel_fro": float(torch.linalg.norm(R32m * sgn[None, :] - R64m) / torch.linalg.norm(R64m)),
+    }
     return out
 
 

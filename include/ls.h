@@ -205,6 +205,19 @@ LS_API ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t
 LS_API ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int nprob, int zeta, int q,
                                   const ls_opts* opts, ls_info* infos);
 
+/* Mixed precision (no counterpart in the paper's experiments; Sec. 3.2 reads
+ * the iteration as iterative refinement, which tolerates a preconditioner R
+ * perturbed by c kappa u32): as ls_solve_batched, but the sketch is summed in
+ * FP32 (each A entry rounded to FP32, FP32 accumulation in the same order,
+ * the scale applied once) and the Householder QR runs in FP32 on one CTA per
+ * problem; R, Q^T S b and everything after them are FP64 (R is the FP32
+ * factor widened).  The FP64 residual and gradient make x as accurate as the
+ * FP64 path; the FP32 R costs iterations (the contraction rate grows with
+ * kappa u32), and beyond kappa(A) ~ 1e6 the iteration may not contract.
+ * B_out receives the FP32 sketch widened to FP64, R_out the widened R. */
+LS_API ls_status ls_solve_batched_mixed(ls_ctx* ctx, const ls_problem* probs, int nprob, int zeta, int q,
+                                        const ls_opts* opts, ls_info* infos);
+
 /* ---------------------------------------------------------------- serving
  * Continuous batching (no counterpart in the paper, which solves one problem
  * at a time): requests are queued by ls_server_submit, admitted in arrival

@@ -98,6 +98,8 @@ def lib():
     L.ls_opts_momentum.argtypes = [C.POINTER(ls_opts), I64, I64]
     L.ls_solve_batched.argtypes = [P, C.POINTER(ls_problem), I, I, I, C.POINTER(ls_opts), C.POINTER(ls_info)]
     L.ls_solve_batched.restype = S
+    L.ls_solve_batched_mixed.argtypes = [P, C.POINTER(ls_problem), I, I, I, C.POINTER(ls_opts), C.POINTER(ls_info)]
+    L.ls_solve_batched_mixed.restype = S
     L.ls_server_request_bytes.argtypes = [I64, I64, I64, I64]
     L.ls_server_request_bytes.restype = C.c_size_t
     L.ls_server_create.argtypes = [P, I, I64, C.c_size_t, C.c_size_t, I, I, C.POINTER(ls_opts), C.POINTER(P)]
@@ -236,9 +238,10 @@ class Context:
         self._check(st, allow=(LS_OK, LS_ENOTCONV))
         return st, info
 
-    def ls_solve_batched(self, probs, zeta, q, opts=None, infos=None):
+    def ls_solve_batched(self, probs, zeta, q, opts=None, infos=None, mixed=False):
         """probs: sequence of ls_problem (or dicts with its fields; tensors are
-        taken by pointer).  Returns the ls_info array (one per problem)."""
+        taken by pointer).  Returns the ls_info array (one per problem).
+        mixed=True calls ls_solve_batched_mixed (FP32 sketch and QR)."""
         arr = (ls_problem * len(probs))()
         for i, p in enumerate(probs):
             if isinstance(p, ls_problem):
@@ -247,9 +250,12 @@ class Context:
             arr[i] = ls_problem(_ptr(p["A"]), _ptr(p["b"]), _ptr(p["x"]), p["m"], p["n"], p["lda"], p["d"],
                                 p.get("seed", i), _ptr(p.get("B_out")), _ptr(p.get("R_out")))
         infos = infos if infos is not None else (ls_info * len(probs))()
-        self._check(lib().ls_solve_batched(self._h, arr, len(probs), zeta, q,
-                                           C.byref(opts) if opts is not None else None, infos))
+        fn = lib().ls_solve_batched_mixed if mixed else lib().ls_solve_batched
+        self._check(fn(self._h, arr, len(probs), zeta, q, C.byref(opts) if opts is not None else None, infos))
         return infos
+
+    def ls_solve_batched_mixed(self, probs, zeta, q, opts=None, infos=None):
+        return self.ls_solve_batched(probs, zeta, q, opts, infos, mixed=True)
 
 
 def server_request_bytes(m, n, lda, d) -> int:

@@ -579,8 +579,12 @@ ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
   return st;
 }
 
-ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zeta, int q, const ls_opts* opts,
-                           ls_info* infos) {
+}  // extern "C"
+
+// The batched solve; mixed = FP32 sketch and QR (one CTA per problem), FP64
+// iteration.
+static ls_status solve_batched_impl(ls_ctx* ctx, const ls_problem* probs, int np, int zeta, int q,
+                                    const ls_opts* opts, ls_info* infos, bool mixed) {
   if (!ctx) return LS_EINVAL;
   ctx->err.clear();
   if (np < 0 || (np > 0 && !probs)) return fail(ctx, LS_EINVAL, "invalid problem array");
@@ -614,15 +618,35 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
   std::vector<int64_t> hoffs(3 * (size_t)np);
   batch_offsets(hp, np, hoffs.data(), hoffs.data() + np, hoffs.data() + 2 * np);
   std::vector<int> horder((size_t)np);
-  const int csize = b_qr_cluster_size(ctx);
+  const int csize = mixed ? 0 : b_qr_cluster_size(ctx);
   const int nsmall = batch_order(hp, np, horder.data(), csize > 0);
+  // mixed: the FP64 stage reads a compact n x (n+1) copy of the factored top rows
+  std::vector<char> hP64;
+  int64_t ctotal = 0;
+  if (mixed) {
+    hP64.assign(hP.begin(), hP.end());
+    BProb* h64 = reinterpret_cast<BProb*>(hP64.data());
+    for (int p = 0; p < np; ++p) {
+      h64[p].d = h64[p].n;
+      h64[p].boff = ctotal;
+      ctotal += h64[p].n * (h64[p].n + 1);
+    }
+  }
 
+  BProb* dP64 = nullptr;
+  float* B32 = nullptr;
+  double* Bc = nullptr;
   auto carve_all = [&](Carve& c, BProb** dP, int64_t** doff3, SketchScratch* sk, BPools* pools, int** dorder,
                        int** alist, int64_t** aoff, int64_t** cnt) {
     *dP = reinterpret_cast<BProb*>(c.take<char>(bprob_bytes() * (size_t)np));
+    if (mixed) {
+      dP64 = reinterpret_cast<BProb*>(c.take<char>(bprob_bytes() * (size_t)np));
+      B32 = c.take<float>((size_t)pl.btotal);
+      Bc = c.take<double>((size_t)ctotal);
+    }
     *doff3 = c.take<int64_t>(3 * (size_t)np);
     *sk = carve_sketch(c, pl.mtotal, pl.dtotal, zeta);
-    pools->B = c.take<double>((size_t)pl.btotal);
+    pools->B = mixed ? nullptr : c.take<double>((size_t)pl.btotal);
     pools->R = c.take<double>((size_t)pl.rtotal);
     pools->V = c.take<double>((size_t)pl.vtotal);
     pools->done_rec = nullptr;
@@ -647,6 +671,8 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
   carve_all(cc, &dP, &doff3, &sk, &pools, &dorder, &alist, &aoff, &cnt);
   if ((st = reset_status(ctx))) return st;
   CUDA_TRY(ctx, cudaMemcpyAsync(dP, hp, bprob_bytes() * (size_t)np, cudaMemcpyHostToDevice, ctx->stream));
+  if (mixed)
+    CUDA_TRY(ctx, cudaMemcpyAsync(dP64, hP64.data(), bprob_bytes() * (size_t)np, cudaMemcpyHostToDevice, ctx->stream));
   CUDA_TRY(ctx, cudaMemcpyAsync(doff3, hoffs.data(), sizeof(int64_t) * 3 * np, cudaMemcpyHostToDevice, ctx->stream));
   CUDA_TRY(ctx, cudaMemcpyAsync(dorder, horder.data(), sizeof(int) * np, cudaMemcpyHostToDevice, ctx->stream));
   CUDA_TRY(ctx, cudaMemsetAsync(pools.pstatus, 0, sizeof(unsigned int) * np, ctx->stream));
@@ -655,7 +681,10 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
   // sketch
   CUDA_TRY(ctx, launch_b_sketch_indices(ctx, dP, doff3, pl, zeta, sk.rows, sk.signs));
-  if (b_csr_fits(pl)) {
+  // one CTA per problem builds small problems' CSR fastest; a problem with
+  // millions of entries would keep one CTA busy for a long time, so batches
+  // holding one use the device-wide counting sort
+  if (b_csr_fits(pl) && pl.max_m * zeta <= b_csr_global_entries()) {
     // buckets above 1024 entries are sorted in global scratch; expect them
     // only when some problem's mean bucket exceeds ~600
     uint32_t* scratch = nullptr;
@@ -669,16 +698,26 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
                                    sk.fill))) {
     return st;
   }
-  CUDA_TRY(ctx, launch_b_gather(ctx, dP, doff3 + 2 * np, pl, sk.row_ptr, sk.ent, 1.0 / std::sqrt((double)zeta),
-                                pools.B));
+  const double scale = 1.0 / std::sqrt((double)zeta);
+  if (mixed)
+    CUDA_TRY(ctx, launch_b_gather32(ctx, dP, doff3 + 2 * np, pl, sk.row_ptr, sk.ent, scale, B32));
+  else
+    CUDA_TRY(ctx, launch_b_gather(ctx, dP, doff3 + 2 * np, pl, sk.row_ptr, sk.ent, scale, pools.B));
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
   for (int p = 0; p < np; ++p)
-    if (probs[p].B_out)
-      CUDA_TRY(ctx, cudaMemcpyAsync(probs[p].B_out, pools.B + batch_boff(hp, p),
-                                    sizeof(double) * (size_t)probs[p].d * (probs[p].n + 1),
-                                    cudaMemcpyDeviceToDevice, ctx->stream));
+    if (probs[p].B_out) {
+      const size_t cntB = (size_t)probs[p].d * (probs[p].n + 1);
+      if (mixed)
+        CUDA_TRY(ctx, launch_widen(ctx, B32 + batch_boff(hp, p), probs[p].B_out, (int64_t)cntB));
+      else
+        CUDA_TRY(ctx, cudaMemcpyAsync(probs[p].B_out, pools.B + batch_boff(hp, p), sizeof(double) * cntB,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    }
   // factor
-  CUDA_TRY(ctx, launch_b_factor2(ctx, dP, dorder, nsmall, dorder + nsmall, np - nsmall, csize, np, nullptr, pools));
+  if (mixed)
+    CUDA_TRY(ctx, launch_b_factor_mixed(ctx, dP, dP64, dorder, np, B32, Bc, pools));
+  else
+    CUDA_TRY(ctx, launch_b_factor2(ctx, dP, dorder, nsmall, dorder + nsmall, np - nsmall, csize, np, nullptr, pools));
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
   for (int p = 0; p < np; ++p)
     if (probs[p].R_out)
@@ -725,6 +764,18 @@ ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zet
     }
   }
   return LS_OK;
+}
+
+extern "C" {
+
+ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zeta, int q, const ls_opts* opts,
+                           ls_info* infos) {
+  return solve_batched_impl(ctx, probs, np, zeta, q, opts, infos, false);
+}
+
+ls_status ls_solve_batched_mixed(ls_ctx* ctx, const ls_problem* probs, int np, int zeta, int q, const ls_opts* opts,
+                                 ls_info* infos) {
+  return solve_batched_impl(ctx, probs, np, zeta, q, opts, infos, true);
 }
 
 ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n, int64_t lda, int64_t d,

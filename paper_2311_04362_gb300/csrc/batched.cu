@@ -220,10 +220,14 @@ __global__ void __launch_bounds__(kCsrThreads) k_b_csr(const BProb* __restrict__
 // B_p[t, c] = s * (left-to-right sum over the bucket of +-[A_p b_p][j, c]).
 // A warp serves 32 / gw buckets of one problem, gw lanes each (one column per
 // lane, column chunks of gw).  Warps are numbered per problem from woffs.
+// F = double: the oracle's sums; F = float: the same order in FP32 (each
+// A entry rounded to FP32, FP32 accumulation, the scale applied in FP64 and
+// the product rounded once to FP32).
+template <typename F>
 __global__ void __launch_bounds__(256) k_b_gather(const BProb* __restrict__ P, const int64_t* __restrict__ woffs,
                                                   int np, int64_t nwarps, const int64_t* __restrict__ row_ptr,
                                                   const uint32_t* __restrict__ ent, double scale,
-                                                  double* __restrict__ Bpool) {
+                                                  F* __restrict__ Bpool) {
   const int64_t wg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (wg >= nwarps) return;
@@ -235,20 +239,20 @@ __global__ void __launch_bounds__(256) k_b_gather(const BProb* __restrict__ P, c
   const int cl = lane % gw;
   const int64_t tg = pr.doff + t;
   const int64_t e0 = row_ptr[tg], e1 = row_ptr[tg + 1];
-  double* B = Bpool + pr.boff;
+  F* B = Bpool + pr.boff;
   const uint32_t mo = (uint32_t)pr.moff;              // entries hold global column ids
   for (int64_t c = cl; c <= pr.n; c += gw) {
     const bool isb = (c == pr.n);
     const double* base = isb ? pr.b : (pr.A + c);
     const int64_t stride = isb ? 1 : pr.lda;
-    double acc = 0.0;
+    F acc = F(0);
     int64_t e = e0;
     for (; e + 4 <= e1; e += 4) {
       const uint32_t n0 = __ldg(ent + e), n1 = __ldg(ent + e + 1), n2 = __ldg(ent + e + 2), n3 = __ldg(ent + e + 3);
-      const double v0 = __ldg(base + (int64_t)((n0 >> 1) - mo) * stride);
-      const double v1 = __ldg(base + (int64_t)((n1 >> 1) - mo) * stride);
-      const double v2 = __ldg(base + (int64_t)((n2 >> 1) - mo) * stride);
-      const double v3 = __ldg(base + (int64_t)((n3 >> 1) - mo) * stride);
+      const F v0 = (F)__ldg(base + (int64_t)((n0 >> 1) - mo) * stride);
+      const F v1 = (F)__ldg(base + (int64_t)((n1 >> 1) - mo) * stride);
+      const F v2 = (F)__ldg(base + (int64_t)((n2 >> 1) - mo) * stride);
+      const F v3 = (F)__ldg(base + (int64_t)((n3 >> 1) - mo) * stride);
       acc = acc + signed_by(v0, n0);
       acc = acc + signed_by(v1, n1);
       acc = acc + signed_by(v2, n2);
@@ -256,10 +260,10 @@ __global__ void __launch_bounds__(256) k_b_gather(const BProb* __restrict__ P, c
     }
     for (; e < e1; ++e) {
       const uint32_t n0 = __ldg(ent + e);
-      const double v0 = __ldg(base + (int64_t)((n0 >> 1) - mo) * stride);
+      const F v0 = (F)__ldg(base + (int64_t)((n0 >> 1) - mo) * stride);
       acc = acc + signed_by(v0, n0);
     }
-    B[t + c * pr.d] = scale * acc;
+    B[t + c * pr.d] = (F)(scale * (double)acc);
   }
 }
 
@@ -275,46 +279,47 @@ __global__ void __launch_bounds__(256) k_b_gather(const BProb* __restrict__ P, c
 static constexpr int kHB = 16;        // panel width
 static constexpr int kHChunk = 64;    // rows of V per shared-memory chunk
 
+template <typename F>
 __global__ void __launch_bounds__(256, 3) k_b_householder(const BProb* __restrict__ P, const int* __restrict__ order,
-                                                       double* __restrict__ Bpool,
+                                                       F* __restrict__ Bpool,
                                                        unsigned int* __restrict__ pstatus) {
-  __shared__ double Vs[kHChunk * kHB];
-  __shared__ double Wp[256 * kHB];
-  __shared__ double T[kHB * kHB];
-  __shared__ double Gs[kHB * kHB];
-  __shared__ double taus[kHB];
-  __shared__ double tmp[kHB];
-  __shared__ double s_par[3];
+  __shared__ F Vs[kHChunk * kHB];
+  __shared__ F Wp[256 * kHB];
+  __shared__ F T[kHB * kHB];
+  __shared__ F Gs[kHB * kHB];
+  __shared__ F taus[kHB];
+  __shared__ F tmp[kHB];
+  __shared__ F s_par[3];
   __shared__ int s_bad;
   const int p = order[blockIdx.x];
   const BProb pr = P[p];
   const int64_t d = pr.d;
   const int n = (int)pr.n;
-  double* B = Bpool + pr.boff;
+  F* B = Bpool + pr.boff;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int k0 = 0; k0 < n; k0 += kHB) {
     const int w = min(kHB, n - k0);
     // ---- panel: columns k0 .. k0 + w - 1, unblocked
     for (int kk = 0; kk < w; ++kk) {
       const int k = k0 + kk;
-      double* col = B + k + (int64_t)k * d;
+      F* col = B + k + (int64_t)k * d;
       const int64_t len = d - k;
-      double ss = 0.0;
+      F ss = F(0);
       for (int64_t i = 1 + tid; i < len; i += 256) ss += col[i] * col[i];
       ss = cta_sum(ss);
       if (tid == 0) {
-        const double alpha = col[0];
-        const double xnorm = sqrt(ss);
-        double beta, tau, scal;
-        if (xnorm == 0.0) { beta = alpha; tau = 0.0; scal = 1.0; }
+        const F alpha = col[0];
+        const F xnorm = sqrt(ss);
+        F beta, tau, scal;
+        if (xnorm == F(0)) { beta = alpha; tau = F(0); scal = F(1); }
         else {
-          const double h = hypot(alpha, xnorm);
-          beta = (alpha >= 0.0) ? -h : h;
+          const F h = hypot(alpha, xnorm);
+          beta = (alpha >= F(0)) ? -h : h;
           tau = (beta - alpha) / beta;
-          scal = 1.0 / (alpha - beta);
+          scal = F(1) / (alpha - beta);
         }
         s_par[0] = beta; s_par[1] = tau; s_par[2] = scal;
-        s_bad = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+        s_bad = (beta == F(0) || !isfinite(beta)) ? 1 : 0;
         taus[kk] = tau;
       }
       __syncthreads();
@@ -322,19 +327,19 @@ __global__ void __launch_bounds__(256, 3) k_b_householder(const BProb* __restric
         if (tid == 0) pstatus[p] |= LS_DEV_RANK;
         return;
       }
-      const double tau = s_par[1], scal = s_par[2];
-      if (tau != 0.0)
+      const F tau = s_par[1], scal = s_par[2];
+      if (tau != F(0))
         for (int64_t i = 1 + tid; i < len; i += 256) col[i] *= scal;
       __syncthreads();
       if (tid == 0) col[0] = s_par[0];
-      if (tau != 0.0) {
+      if (tau != F(0)) {
         for (int j = k + 1 + warp; j < k0 + w; j += 8) {
-          double* cj = B + k + (int64_t)j * d;
-          double acc = 0.0;
-          for (int64_t i = lane; i < len; i += 32) acc += ((i == 0) ? 1.0 : col[i]) * cj[i];
+          F* cj = B + k + (int64_t)j * d;
+          F acc = F(0);
+          for (int64_t i = lane; i < len; i += 32) acc += ((i == 0) ? F(1) : col[i]) * cj[i];
           acc = warp_sum(acc);
-          const double tw = tau * acc;
-          for (int64_t i = lane; i < len; i += 32) cj[i] = cj[i] - tw * ((i == 0) ? 1.0 : col[i]);
+          const F tw = tau * acc;
+          for (int64_t i = lane; i < len; i += 32) cj[i] = cj[i] - tw * ((i == 0) ? F(1) : col[i]);
         }
       }
       __syncthreads();
@@ -347,19 +352,19 @@ __global__ void __launch_bounds__(256, 3) k_b_householder(const BProb* __restric
       int a = 0, rem = pi;
       while (rem >= w - 1 - a) { rem -= w - 1 - a; ++a; }
       const int b = a + 1 + rem;
-      const double* va = B + (int64_t)(k0 + a) * d;
-      const double* vb = B + (int64_t)(k0 + b) * d;
-      double acc = 0.0;
-      for (int64_t i = k0 + b + lane; i < d; i += 32) acc += va[i] * ((i == k0 + b) ? 1.0 : vb[i]);
+      const F* va = B + (int64_t)(k0 + a) * d;
+      const F* vb = B + (int64_t)(k0 + b) * d;
+      F acc = F(0);
+      for (int64_t i = k0 + b + lane; i < d; i += 32) acc += va[i] * ((i == k0 + b) ? F(1) : vb[i]);
       acc = warp_sum(acc);
       if (lane == 0) Gs[a * kHB + b] = acc;
     }
-    if (tid < kHB * kHB) T[tid] = 0.0;
+    if (tid < kHB * kHB) T[tid] = F(0);
     __syncthreads();
     // ---- T (upper): T[kk][kk] = tau_kk, T[0:kk, kk] = -tau_kk T[0:kk, 0:kk] G[0:kk, kk]
     for (int kk = 0; kk < w; ++kk) {
       if (tid < kk) {
-        double t = 0.0;
+        F t = F(0);
         for (int c = tid; c < kk; ++c) t += T[tid * kHB + c] * Gs[c * kHB + kk];
         tmp[tid] = -taus[kk] * t;
       }
@@ -374,18 +379,18 @@ __global__ void __launch_bounds__(256, 3) k_b_householder(const BProb* __restric
       const int Gr = max(1, 256 / nc);
       const int g = tid / nc, jl = tid - g * nc;
       const bool active = g < Gr;
-      double* cj = B + (int64_t)(j0 + cb + jl) * d;
-      double acc[kHB];
+      F* cj = B + (int64_t)(j0 + cb + jl) * d;
+      F acc[kHB];
 #pragma unroll
-      for (int q = 0; q < kHB; ++q) acc[q] = 0.0;
+      for (int q = 0; q < kHB; ++q) acc[q] = F(0);
       for (int pass = 0; pass < 2; ++pass) {
         for (int64_t r0 = k0; r0 < d; r0 += kHChunk) {
           const int h = (int)min((int64_t)kHChunk, d - r0);
           for (int e = tid; e < h * kHB; e += 256) {
             const int i = e / kHB, q = e - i * kHB;
             const int64_t R = r0 + i, dq = k0 + q;
-            double v = 0.0;
-            if (q < w) v = (R < dq) ? 0.0 : (R == dq ? 1.0 : B[R + dq * d]);
+            F v = F(0);
+            if (q < w) v = (R < dq) ? F(0) : (R == dq ? F(1) : B[R + dq * d]);
             Vs[e] = v;
           }
           __syncthreads();
@@ -394,15 +399,15 @@ __global__ void __launch_bounds__(256, 3) k_b_householder(const BProb* __restric
             const int i0 = g * rpg, i1 = min(h, i0 + rpg);
             if (pass == 0) {
               for (int i = i0; i < i1; ++i) {
-                const double c = cj[r0 + i];
-                const double* vr = Vs + i * kHB;
+                const F c = cj[r0 + i];
+                const F* vr = Vs + i * kHB;
 #pragma unroll
                 for (int q = 0; q < kHB; ++q) acc[q] = fma(vr[q], c, acc[q]);
               }
             } else {
               for (int i = i0; i < i1; ++i) {
-                double c = cj[r0 + i];
-                const double* vr = Vs + i * kHB;
+                F c = cj[r0 + i];
+                const F* vr = Vs + i * kHB;
 #pragma unroll
                 for (int q = 0; q < kHB; ++q) c = fma(-vr[q], acc[q], c);
                 cj[r0 + i] = c;
@@ -419,16 +424,16 @@ __global__ void __launch_bounds__(256, 3) k_b_householder(const BProb* __restric
             for (int q = 0; q < kHB; ++q) Wp[(g * nc + jl) * kHB + q] = acc[q];
           __syncthreads();
           if (active && g == 0) {
-            double wv[kHB];
+            F wv[kHB];
 #pragma unroll
             for (int q = 0; q < kHB; ++q) {
-              double t = 0.0;
+              F t = F(0);
               for (int gg = 0; gg < Gr; ++gg) t += Wp[(gg * nc + jl) * kHB + q];
               wv[q] = t;
             }
 #pragma unroll
             for (int q = 0; q < kHB; ++q) {
-              double y = 0.0;
+              F y = F(0);
 #pragma unroll
               for (int a = 0; a <= q; ++a) y = fma(T[a * kHB + q], wv[a], y);
               acc[q] = y;
@@ -683,6 +688,27 @@ __global__ void __launch_bounds__(256, 1) k_b_qr_cluster(const BProb* __restrict
     }
   }
   cluster_sync();                                  // no CTA leaves while others read its shared memory
+}
+
+// Mixed precision: the top n rows of each problem's FP32-factored sketch (R
+// on and above the diagonal, (Q^T S b)[0:n] in column n), widened to FP64
+// into a compact n x (n+1) block at P64[p].boff (leading dimension n).
+__global__ void k_b_widen_top(const BProb* __restrict__ P, const BProb* __restrict__ P64, int np,
+                              const float* __restrict__ B32, double* __restrict__ Bc) {
+  for (int p = blockIdx.x; p < np; p += gridDim.x) {
+    const int64_t n = P[p].n, d = P[p].d;
+    const float* src = B32 + P[p].boff;
+    double* dst = Bc + P64[p].boff;
+    for (int64_t e = threadIdx.x; e < n * (n + 1); e += blockDim.x) {
+      const int64_t c = e / n, i = e - c * n;
+      dst[i + c * n] = (double)src[i + c * d];
+    }
+  }
+}
+
+__global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
 }
 
 // R_p, R_p^T and 1/diag(R_p) of the listed problems (all when list is null).
@@ -1242,7 +1268,7 @@ cudaError_t launch_b_sketch_indices(ls_ctx* ctx, const BProb* dP, const int64_t*
 
 cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* dwoffs, const BatchPlan& pl,
                             const int64_t* row_ptr, const uint32_t* ent, double scale, double* Bpool) {
-  k_b_gather<<<(unsigned)((pl.wtotal + 7) / 8), 256, 0, ctx->stream>>>(dP, dwoffs, pl.np, pl.wtotal, row_ptr, ent,
+  k_b_gather<double><<<(unsigned)((pl.wtotal + 7) / 8), 256, 0, ctx->stream>>>(dP, dwoffs, pl.np, pl.wtotal, row_ptr, ent,
                                                                        scale, Bpool);
   ++ctx->launches;
   return cudaGetLastError();
@@ -1250,6 +1276,7 @@ cudaError_t launch_b_gather(ls_ctx* ctx, const BProb* dP, const int64_t* dwoffs,
 
 bool b_csr_fits(const BatchPlan& pl) { return pl.max_d <= kCsrMaxD; }
 int64_t b_csr_max_d() { return kCsrMaxD; }
+int64_t b_csr_global_entries() { return (int64_t)1 << 18; }
 
 cudaError_t launch_b_csr(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, int zeta, const int32_t* rows,
                          const uint32_t* signs, int64_t* row_ptr, uint32_t* ent, uint32_t* scratch) {
@@ -1342,7 +1369,7 @@ cudaError_t launch_b_factor2(ls_ctx* ctx, const BProb* dP, const int* dorder, in
   cudaError_t e;
   if (nbig > 0 && (e = launch_b_qr_cluster(ctx, dP, dbig, nbig, csize, pools)) != cudaSuccess) return e;
   if (nsmall > 0) {
-    k_b_householder<<<nsmall, 256, 0, ctx->stream>>>(dP, dorder, pools.B, pools.pstatus);
+    k_b_householder<double><<<nsmall, 256, 0, ctx->stream>>>(dP, dorder, pools.B, pools.pstatus);
     ++ctx->launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -1356,9 +1383,47 @@ cudaError_t launch_b_factor2(ls_ctx* ctx, const BProb* dP, const int* dorder, in
   return launch_cluster_grid(ctx, (const void*)k_b_post_factor, args, count);
 }
 
+cudaError_t launch_b_gather32(ls_ctx* ctx, const BProb* dP, const int64_t* dwoffs, const BatchPlan& pl,
+                              const int64_t* row_ptr, const uint32_t* ent, double scale, float* B32) {
+  k_b_gather<float><<<(unsigned)((pl.wtotal + 7) / 8), 256, 0, ctx->stream>>>(dP, dwoffs, pl.np, pl.wtotal, row_ptr,
+                                                                              ent, scale, B32);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+// FP32 factorization of every problem (one CTA each, in dorder), then the
+// FP64 R, R^T, x0 and estimates from the widened top rows (dP64: d = n,
+// boff into Bc).
+cudaError_t launch_b_factor_mixed(ls_ctx* ctx, const BProb* dP, const BProb* dP64, const int* dorder, int np,
+                                  float* B32, double* Bc, const BPools& pools) {
+  k_b_householder<float><<<np, 256, 0, ctx->stream>>>(dP, dorder, B32, pools.pstatus);
+  ++ctx->launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_b_widen_top<<<std::min(np, ctx->num_sms * 8), 256, 0, ctx->stream>>>(dP, dP64, np, B32, Bc);
+  ++ctx->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  BPools p64 = pools;
+  p64.B = Bc;
+  k_b_prepare_R<<<std::min(np, ctx->num_sms * 8), 256, 0, ctx->stream>>>(dP64, nullptr, np, p64);
+  ++ctx->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const BProb* dPP = dP64;
+  const int* lp = nullptr;
+  void* args[] = {(void*)&dPP, (void*)&lp, &p64};
+  return launch_cluster_grid(ctx, (const void*)k_b_post_factor, args, np);
+}
+
+cudaError_t launch_widen(ls_ctx* ctx, const float* src, double* dst, int64_t count) {
+  k_widen<<<(unsigned)std::min<int64_t>((count + 255) / 256, (int64_t)ctx->num_sms * 8), 256, 0, ctx->stream>>>(
+      src, dst, count);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_b_factor(ls_ctx* ctx, const BProb* dP, const int* dorder, int count, const int* list,
                             const BPools& pools) {
-  k_b_householder<<<count, 256, 0, ctx->stream>>>(dP, dorder, pools.B, pools.pstatus);
+  k_b_householder<double><<<count, 256, 0, ctx->stream>>>(dP, dorder, pools.B, pools.pstatus);
   ++ctx->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

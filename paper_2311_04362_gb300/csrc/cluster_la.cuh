@@ -50,6 +50,25 @@ __device__ inline double cta_sum(double v) {
   return s;
 }
 
+__device__ inline float cta_sum(float v) {
+  __shared__ float red32[32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red32[w] = v;
+  __syncthreads();
+  float s = 0.0f;
+  if (w == 0) {
+    s = (l < (int)(blockDim.x >> 5)) ? red32[l] : 0.0f;
+    s = warp_sum(s);
+    if (l == 0) red32[0] = s;
+  }
+  __syncthreads();
+  s = red32[0];
+  __syncthreads();
+  return s;
+}
+
 __device__ inline double cta_max(double v) {
   __shared__ double red[32];
 #pragma unroll

@@ -211,6 +211,9 @@ __device__ inline bool grid_sync(const GridBar& gb, unsigned int nblocks) {
 __device__ inline double signed_by(double v, uint32_t en) {
   return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(en & 1u) << 63));
 }
+__device__ inline float signed_by(float v, uint32_t en) {
+  return __int_as_float(__float_as_int(v) ^ (int)((en & 1u) << 31));
+}
 
 // ------------------------------------------------------------ reductions
 // Block-wide bitonic sort of s[0..P) ascending (P a power of two; every
@@ -232,6 +235,11 @@ __device__ inline void bitonic(uint32_t* s, int P) {
 }
 
 __device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -396,6 +404,7 @@ struct BatchPlan {
   double max_fill;               // largest m / d (mean bucket size / zeta)
 };
 bool b_csr_fits(const BatchPlan& pl);
+int64_t b_csr_global_entries();
 cudaError_t launch_b_csr(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, int zeta, const int32_t* rows,
                          const uint32_t* signs, int64_t* row_ptr, uint32_t* ent, uint32_t* scratch);
 size_t bprob_bytes();
@@ -414,6 +423,11 @@ int b_qr_cluster_size(ls_ctx* ctx);
 int b_qr_cluster_max_n();
 cudaError_t launch_b_factor2(ls_ctx* ctx, const BProb* dP, const int* dorder, int nsmall, const int* dbig, int nbig,
                              int csize, int count, const int* list, const BPools& pools);
+cudaError_t launch_b_gather32(ls_ctx* ctx, const BProb* dP, const int64_t* dwoffs, const BatchPlan& pl,
+                              const int64_t* row_ptr, const uint32_t* ent, double scale, float* B32);
+cudaError_t launch_b_factor_mixed(ls_ctx* ctx, const BProb* dP, const BProb* dP64, const int* dorder, int np,
+                                  float* B32, double* Bc, const BPools& pools);
+cudaError_t launch_widen(ls_ctx* ctx, const float* src, double* dst, int64_t count);
 cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, int count, const int* list, const BPools& pools,
                                double gamma, double rho, double alpha, double beta);
 cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, int np, const BPools& pools, int* alist, int64_t* aoff,

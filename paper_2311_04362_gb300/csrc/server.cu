@@ -34,7 +34,6 @@
 using namespace lsk;
 
 namespace lsk {
-bool b_csr_fits(const BatchPlan& pl);
 int64_t b_csr_max_d();
 }  // namespace lsk
 
@@ -89,7 +88,6 @@ class FirstFit {
 
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-constexpr int64_t kCsrGlobalEntries = 1 << 18;   // entries of one problem above which the CSR is device-wide
 
 struct Layout {   // byte offsets within a request's workspace region
   size_t B, R, V, part, rprev, total;
@@ -298,7 +296,7 @@ ls_status admit(ls_server* s, int* kout) {
   // one CTA per problem builds small problems' CSR fastest; a problem with
   // millions of entries would keep its CTA busy for tens of milliseconds, so
   // batches holding one go through the device-wide counting sort instead
-  const bool global_csr = (int64_t)pl.max_m * s->zeta > kCsrGlobalEntries;
+  const bool global_csr = (int64_t)pl.max_m * s->zeta > b_csr_global_entries();
   uint32_t* scratch = nullptr;
   if (global_csr || pl.max_fill * s->zeta > 600.0) {
     SRV_CUDA(s, grow(&s->sort_scratch, &s->cap_scratch, 2 * entries));

@@ -96,6 +96,8 @@ def make_problem_torch(m: int, n: int, kappa: float, resnorm: float, seed: int, 
 # The paper-shaped configurations (Sec. 1.1.1; Sec. 3.3: d = 20 n, zeta = 8).
 SMALL = dict(m=4000, n=50, kappa=1e10, resnorm=1e-6, d=1000, zeta=8, seed=0, q=100)
 LARGE = dict(m=2_000_000, n=1000, kappa=1e8, resnorm=1e-4, d=20_000, zeta=8, seed=0, q=100)
+# Mixed-precision comparison problem.
+MIXED = dict(m=1_000_000, n=200, kappa=1e4, resnorm=1e-3, d=4000, zeta=8, seed=0, q=100)
 
 
 # Batched uneven problems (4096 independent problems, Sec. 1.1.1 construction
