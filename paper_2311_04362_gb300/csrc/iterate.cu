@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constan
   double* xs = tiles + S * stage_doubles;
   double* rtile = xs + ((n + 1) & ~1);
   double* red = rtile + 2 * tr;                     // 2 * kConsumerWarps + 8
-  uint64_t* full = reinterpret_cast<uint64_t*>(red + 2 * kConsumerWarps + 8);
+  double* p1 = red + 2 * kConsumerWarps + 8;         // kConsumerWarps * 8 row-dot partials (n > 256)
+  uint64_t* full = reinterpret_cast<uint64_t*>(p1 + kConsumerWarps * 8);
   uint64_t* empty = full + S;
   __shared__ int s_abort;
 
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constan
   double acc[NPT];
 #pragma unroll
   for (int u = 0; u < NPT; ++u) acc[u] = 0.0;
-  double rn2 = 0.0, dn2 = 0.0;               // lane-0 accumulators per warp
+  double rn2 = 0.0, dn2 = 0.0;               // per-thread accumulators (rows this thread finishes)
   const int g = tid / max(n, 1);             // phase-2 row group (n < 256)
   const int cg = tid - g * n;                // phase-2 column (n < 256)
 
@@ -115,6 +116,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constan
     const int64_t row0 = (int64_t)t * tr;
     const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
 
+    if (nbox > 1) {
+      // phase 1 (n > 256, tr = 8 or 4): every warp takes all tr rows, LPR =
+      // 32 / tr lanes per row; lane (r, q) of warp w sums the columns
+      // c = LPR ((w + r) mod 8) + q (mod 8 LPR) -- each row's columns are
+      // covered once over the 8 warps, and the rotation by r puts the rows of
+      // a warp on different banks.  The LPR lanes are combined by shuffles,
+      // the 8 warps in warp order by one thread per row.  Per row this costs
+      // ~3.5 FP64 instructions besides the FMAs, against 9 for a warp per row
+      // (a 5-level shuffle tree and the row's scalar work on one lane).
+      const int LPR = 32 / tr, CS = 8 * LPR;
+      const int r = lane / LPR, q = lane - r * LPR;
+      double bj = 0.0, rpj = 0.0;
+      if (tid < rows) {                       // issue the row's loads before the dots
+        bj = a.b[row0 + tid];
+        if (a.r_prev) rpj = a.r_prev[row0 + tid];
+      }
+      double dot = 0.0;
+      if (r < rows)
+        for (int c = LPR * ((warp + r) & 7) + q; c < n; c += CS) dot += tl[tile_off(r, c, boxw, nbox, tr)] * xs[c];
+      for (int o = LPR >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      if (q == 0) p1[warp * tr + r] = dot;
+      asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32));
+      if (tid < tr) {
+        double rj = 0.0;
+        if (tid < rows) {
+          double d = 0.0;
+#pragma unroll
+          for (int w = 0; w < kConsumerWarps; ++w) d += p1[w * tr + tid];
+          rj = bj - d;
+          rn2 += rj * rj;
+          if (a.r_prev) { const double dl = rj - rpj; dn2 += dl * dl; }
+          if (a.r_out) a.r_out[row0 + tid] = rj;
+        }
+        rt[tid] = rj;
+      }
+    } else
     // phase 1: r_j = b_j - A_j x, one warp per row
     for (int r = warp; r < tr; r += kConsumerWarps) {
       double dot = 0.0, bj = 0.0, rpj = 0.0;
@@ -178,6 +215,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constan
       out[c] = sum;
     }
   }
+  rn2 = warp_sum(rn2);
+  dn2 = warp_sum(dn2);
   if (lane == 0) { red[warp] = rn2; red[kConsumerWarps + warp] = dn2; }
   asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32));
   if (tid == 0) {
@@ -312,7 +351,7 @@ PassGeom pass_geometry(const ls_ctx* ctx, int64_t n, int64_t m) {
   const int64_t ntiles = (m + g.tr - 1) / g.tr;
   g.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ntiles));
   g.smem = g.stages * stage + (size_t)((n + 1) & ~1LL) * 8 + 2 * g.tr * 8 + (2 * kConsumerWarps + 8) * 8 +
-           2 * g.stages * 8 + 128;
+           kConsumerWarps * 8 * 8 + 2 * g.stages * 8 + 128;
   // phase-2 group sums for n < 256 reuse the tile memory
   return g;
 }
