@@ -190,13 +190,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the damping / momentum timings")
     ap.add_argument("--check-qr", action="store_true", help="also compute the Householder-QR forward error (slow)")
-    ap.add_argument("--case", choices=["solve", "pass", "sketch"], default="solve",
+    ap.add_argument("--count", type=int, default=None, help="problems for --case batched / serve")
+    ap.add_argument("--q", type=int, default=None, help="iterations for --case batched (stopping rule off)")
+    ap.add_argument("--case", choices=["solve", "pass", "sketch", "batched", "serve"], default="solve",
                     help="pass / sketch: only the fused residual/gradient pass, or only the sketch B = S[A b], "
                          "on an m x 1000 problem (for ncu captures)")
     ap.add_argument("--m", type=int, default=200_000, help="rows for --case pass")
+    ap.add_argument("--n", type=int, default=1000, help="columns for --case pass")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-problems timing")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) sweep")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
+    ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-A workload")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -209,6 +213,10 @@ def main():
         return pass_case(args)
     if args.case == "sketch":
         return sketch_case(args)
+    if args.case == "batched":
+        return batched_profile_case(args)
+    if args.case == "serve":
+        return serve_profile_case(args)
 
     import numpy as np
     import torch
@@ -329,6 +337,10 @@ def main():
     if not args.no_mixed:
         mixed = mixed_case(ctx, stream, args, pg, world)
 
+    sparse = None
+    if not args.no_sparse:
+        sparse = sparse_case(ctx, stream, args, pg, world)
+
     fe_qr = None
     if args.check_qr and rank == 0:
         import oracle
@@ -364,6 +376,7 @@ def main():
             "batched": batched,
             "serving": serving,
             "mixed_precision": mixed,
+            "sparse": sparse,
             "phase_ms": {"sketch": statistics.mean(i.ms_sketch for _, i in infos),
                          "factor": statistics.mean(i.ms_factor for _, i in infos),
                          "iterate": statistics.mean(i.ms_iterate for _, i in infos)},
@@ -586,19 +599,119 @@ def mixed_case(ctx, stream, args, pg, world):
     return out
 
 
+def batched_profile_case(args):
+    """One ls_solve_batched call on problems.BATCH (--count problems, default
+    4096) with the stopping rule off for --q iterations (default 3): a fixed
+    amount of work per kernel, for launch lists and ncu captures."""
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    import problems
+    from paper_2311_04362_gb300 import build
+
+    build.build()
+    cfg = dict(problems.BATCH, count=args.count or problems.BATCH["count"])
+    probs = problems.make_batch_torch(problems.batch_shapes(**cfg))
+    o = ls.default_opts()
+    o.use_stop = 0
+    with ls.Context(0, torch.cuda.current_stream()) as ctx:
+        infos = ctx.ls_solve_batched(probs, cfg["zeta"], args.q or 3, o)
+        torch.cuda.synchronize()
+    print(json.dumps({"case": "batched", "problems": len(probs), "q": args.q or 3, "ms_sketch": infos[0].ms_sketch,
+                      "ms_factor": infos[0].ms_factor, "ms_iterate": infos[0].ms_iterate,
+                      "launches": infos[0].launches}))
+
+
+def serve_profile_case(args):
+    """--count problems of problems.SERVE (default 48) submitted at once to a
+    server, stepped until all finish: one admission batch, then the
+    iteration steps.  Prints the step times (host clock)."""
+    import numpy as np
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    import problems
+    from paper_2311_04362_gb300 import build
+
+    build.build()
+    cfg = dict(problems.SERVE, count=args.count or 48)
+    pool = problems.make_batch_torch(problems.batch_shapes(**cfg))
+    torch.cuda.synchronize()
+    with ls.Context(0, torch.cuda.current_stream()) as ctx:
+        srv = ls.Server(ctx, 1024, 512, 16 * 2**30, cfg["budget_bytes"], cfg["zeta"], cfg["q"])
+        t0 = time.perf_counter()
+        for p in pool:
+            srv.ls_server_submit(p)
+        done, steps = 0, []
+        while done < len(pool):
+            a = time.perf_counter()
+            srv.ls_server_step()
+            steps.append(time.perf_counter() - a)
+            done += len(srv.ls_server_poll())
+        total = time.perf_counter() - t0
+        srv.close()
+    print(json.dumps({"case": "serve", "requests": len(pool), "total_s": total, "steps": len(steps),
+                      "first_step_ms": 1e3 * steps[0], "median_step_ms": 1e3 * float(np.median(steps))}))
+
+
+def sparse_case(ctx, stream, args, pg, world):
+    """The sparse workload of Sec. 3.5 (problems.SPARSE: m = 3e6, 3 nonzeros
+    per row, n = 500, d = 30 n) through ls_solve_sparse: solves/s, phases,
+    and the distance to a Householder-QR solution of the densified matrix
+    (geqrf through torch)."""
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    import problems
+
+    cfg = problems.SPARSE
+    m, n = cfg["m"], cfg["n"]
+    d = cfg["d_over_n"] * n
+    S = problems.make_sparse(m, n, cfg["seed"], cfg["nnz_per_row"])
+    rp, col, val, b = (torch.from_numpy(S[k]).cuda() for k in ("row_ptr", "col", "val", "b"))
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.ls_solve_sparse(rp, col, val, m, n, S["nnz"], b, d, cfg["zeta"], cfg["q"], cfg["seed"], x)   # warm
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        st, inf = ctx.ls_solve_sparse(rp, col, val, m, n, S["nnz"], b, d, cfg["zeta"], cfg["q"], cfg["seed"], x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+    A = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    rows = torch.repeat_interleave(torch.arange(m, device="cuda"), torch.diff(rp))
+    A[rows, col.long()] = val
+    t0 = time.perf_counter()
+    Q, R = torch.linalg.qr(A)
+    xq = torch.linalg.solve_triangular(R, (Q.T @ b)[:, None], upper=True)[:, 0]
+    torch.cuda.synchronize()
+    tq = time.perf_counter() - t0
+    rel = float(torch.linalg.norm(x - xq) / torch.linalg.norm(xq))
+    del A, Q, R
+    torch.cuda.empty_cache()
+    return {"workload": "m=3,000,000, 3 nonzeros per row in random columns, values +-1, Gaussian b, n=500, "
+                        "d=30n=15000, zeta=8, seed 0, q <= 100",
+            "value": job_throughput(world, steps, ms), "unit": UNIT, "iters": inf.iters,
+            "stop_reason": inf.stop_reason, "rel_diff_to_qr": rel,
+            "phase_ms": {"sketch": inf.ms_sketch, "factor": inf.ms_factor, "iterate": inf.ms_iterate},
+            "dense_qr_solve_s": tq}
+
+
 def pass_case(args):
-    """Fused residual/gradient passes on an m x 1000 row-major A (default
-    m = 200,000: 1.6 GB, larger than L2) inside ls_iterate (R = s I, a stable
-    Richardson step, stopping rule off).  Each pass is timed by CUDA events
-    on its stream inside the library.  Used for small-case ncu captures of
-    k_fused_pass."""
+    """Fused residual/gradient passes on an m x n row-major A (default
+    m = 200,000, n = 1000: 1.6 GB, larger than L2; n even) inside ls_iterate
+    (R = s I, a stable Richardson step, stopping rule off).  Each pass is
+    timed by CUDA events on its stream inside the library.  Used for
+    small-case ncu captures of k_fused_pass."""
     import torch
 
     import paper_2311_04362_gb300 as ls
     from paper_2311_04362_gb300 import build
 
     build.build()
-    m, n = args.m, 1000
+    m, n = args.m, args.n
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     A = torch.randn(m, n, dtype=torch.float64, device="cuda", generator=g)

@@ -205,6 +205,22 @@ LS_API ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t
 LS_API ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int nprob, int zeta, int q,
                                   const ls_opts* opts, ls_info* infos);
 
+/* Sparse A (Sec. 3.5: a few nonzeros per row): Algorithm 2 with the Sec. 3.3
+ * stopping rule for A in CSR form -- row_ptr (m+1, int64), col (nnz, int32,
+ * distinct within a row), val (nnz) -- and b (m); all device pointers.  The
+ * sketch [S A, S b] is bit-identical to ls_sketch of the dense matrix; the QR
+ * is the dense one; the residual/gradient pass reads A row-wise for A x and a
+ * deterministic CSC copy (built here, nnz * 12 bytes of scratch) for A^T r.
+ * x: n (device, output).  n <= 2048, nnz < 2^31.  Errors as ls_solve_ex
+ * (LS_ERANK for a zero column, LS_ENOTCONV when q is reached).
+ * ls_sketch_sparse: the sketch step alone, B (d x (n+1), column-major, ldb). */
+LS_API ls_status ls_sketch_sparse(ls_ctx* ctx, const int64_t* row_ptr, const int32_t* col, const double* val,
+                                  int64_t m, int64_t n, const double* b, int64_t d, int zeta, uint64_t seed, double* B,
+                                  int64_t ldb);
+LS_API ls_status ls_solve_sparse(ls_ctx* ctx, const int64_t* row_ptr, const int32_t* col, const double* val,
+                                 int64_t m, int64_t n, int64_t nnz, const double* b, int64_t d, int zeta, int q,
+                                 uint64_t seed, const ls_opts* opts, double* x, ls_info* info);
+
 /* Mixed precision (no counterpart in the paper's experiments; Sec. 3.2 reads
  * the iteration as iterative refinement, which tolerates a preconditioner R
  * perturbed by c kappa u32): as ls_solve_batched, but the sketch is summed in

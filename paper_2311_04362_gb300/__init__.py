@@ -100,6 +100,11 @@ def lib():
     L.ls_solve_batched.restype = S
     L.ls_solve_batched_mixed.argtypes = [P, C.POINTER(ls_problem), I, I, I, C.POINTER(ls_opts), C.POINTER(ls_info)]
     L.ls_solve_batched_mixed.restype = S
+    L.ls_sketch_sparse.argtypes = [P, P, P, P, I64, I64, P, I64, I, C.c_uint64, P, I64]
+    L.ls_sketch_sparse.restype = S
+    L.ls_solve_sparse.argtypes = [P, P, P, P, I64, I64, I64, P, I64, I, I, C.c_uint64, C.POINTER(ls_opts), P,
+                                  C.POINTER(ls_info)]
+    L.ls_solve_sparse.restype = S
     L.ls_server_request_bytes.argtypes = [I64, I64, I64, I64]
     L.ls_server_request_bytes.restype = C.c_size_t
     L.ls_server_create.argtypes = [P, I, I64, C.c_size_t, C.c_size_t, I, I, C.POINTER(ls_opts), C.POINTER(P)]
@@ -229,6 +234,17 @@ class Context:
         info = info if info is not None else ls_info()
         st = lib().ls_solve_ex(self._h, _ptr(A), _ptr(b), m, n, lda, d, zeta, q, seed,
                                C.byref(opts) if opts is not None else None, _ptr(x), C.byref(info))
+        self._check(st, allow=(LS_OK, LS_ENOTCONV))
+        return st, info
+
+    def ls_sketch_sparse(self, row_ptr, col, val, m, n, b, d, zeta, seed, B, ldb):
+        return self._check(lib().ls_sketch_sparse(self._h, _ptr(row_ptr), _ptr(col), _ptr(val), m, n, _ptr(b), d,
+                                                  zeta, seed, _ptr(B), ldb))
+
+    def ls_solve_sparse(self, row_ptr, col, val, m, n, nnz, b, d, zeta, q, seed, x, opts=None, info=None):
+        info = info if info is not None else ls_info()
+        st = lib().ls_solve_sparse(self._h, _ptr(row_ptr), _ptr(col), _ptr(val), m, n, nnz, _ptr(b), d, zeta, q,
+                                   seed, C.byref(opts) if opts is not None else None, _ptr(x), C.byref(info))
         self._check(st, allow=(LS_OK, LS_ENOTCONV))
         return st, info
 

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libls.so")
-SOURCES = ["sketch.cu", "factor.cu", "iterate.cu", "batched.cu", "server.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["sketch.cu", "factor.cu", "iterate.cu", "batched.cu", "server.cu", "sparse.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

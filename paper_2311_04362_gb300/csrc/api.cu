@@ -778,6 +778,150 @@ ls_status ls_solve_batched_mixed(ls_ctx* ctx, const ls_problem* probs, int np, i
   return solve_batched_impl(ctx, probs, np, zeta, q, opts, infos, true);
 }
 
+ls_status ls_sketch_sparse(ls_ctx* ctx, const int64_t* row_ptr, const int32_t* col, const double* val, int64_t m,
+                           int64_t n, const double* b, int64_t d, int zeta, uint64_t seed, double* B, int64_t ldb) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st;
+  if ((st = check_sketch_args(ctx, m, d, zeta))) return st;
+  if (!row_ptr || !col || !val || !b || !B) return fail(ctx, LS_EINVAL, "null pointer argument");
+  if (n < 1 || n > kMaxN) return fail(ctx, LS_EINVAL, "need 1 <= n <= %lld", (long long)kMaxN);
+  if (ldb < d) return fail(ctx, LS_EINVAL, "ldb < d");
+  cudaSetDevice(ctx->device);
+  Carve probe(nullptr);
+  carve_sketch(probe, m, d, zeta);
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  if ((st = reset_status(ctx))) return st;
+  SketchScratch sk = carve_sketch(cc, m, d, zeta);
+  CUDA_TRY(ctx, launch_sketch_indices(ctx, m, d, zeta, seed, sk.rows, sk.signs));
+  if ((st = sketch_csr_impl(ctx, m, d, zeta, sk.rows, sk.signs, sk.row_ptr, sk.ent, sk.fill))) return st;
+  CUDA_TRY(ctx, launch_sp_gather(ctx, d, sk.row_ptr, sk.ent, row_ptr, col, val, b, n, 1.0 / std::sqrt((double)zeta),
+                                 B, ldb));
+  return sync_and_check(ctx);
+}
+
+ls_status ls_solve_sparse(ls_ctx* ctx, const int64_t* row_ptr, const int32_t* col, const double* val, int64_t m,
+                          int64_t n, int64_t nnz, const double* b, int64_t d, int zeta, int q, uint64_t seed,
+                          const ls_opts* opts, double* x, ls_info* info) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st;
+  if ((st = check_sketch_args(ctx, m, d, zeta))) return st;
+  if (!row_ptr || !col || !val || !b || !x) return fail(ctx, LS_EINVAL, "null pointer argument");
+  if (n < 1 || n > m) return fail(ctx, LS_EINVAL, "need 1 <= n <= m");
+  if (n > kMaxN) return fail(ctx, LS_EINVAL, "n = %lld above the limit %lld", (long long)n, (long long)kMaxN);
+  if (d < n) return fail(ctx, LS_EINVAL, "d must be >= n");
+  if (nnz < 1 || nnz > INT32_MAX) return fail(ctx, LS_EINVAL, "nnz out of range");
+  if (q <= 0) q = 100;
+  ls_opts o;
+  ls_default_opts(&o);
+  if (opts) o = *opts;
+  cudaSetDevice(ctx->device);
+  const int64_t nb = sp_blocks(m);
+  const int g = sp_residual_grid(ctx), segs = sp_segments(ctx, n);
+  auto carve = [&](Carve& c, double** B, double** R, int32_t** cnt, int64_t** total, int64_t** col_ptr,
+                   int32_t** crow, double** cval, double** norms_part, double** cpart, double** out) {
+    *B = c.take<double>((size_t)d * (n + 1));
+    *R = c.take<double>((size_t)n * n);
+    *cnt = c.take<int32_t>((size_t)nb * n);
+    *total = c.take<int64_t>((size_t)n);
+    *col_ptr = c.take<int64_t>((size_t)n + 1);
+    *crow = c.take<int32_t>((size_t)nnz);
+    *cval = c.take<double>((size_t)nnz);
+    *norms_part = c.take<double>(2 * (size_t)g);
+    *cpart = c.take<double>((size_t)segs * n);
+    *out = c.take<double>((size_t)n + 2);
+  };
+  double *B, *R, *cval, *norms_part, *cpart, *outp;
+  int32_t *cnt, *crow;
+  int64_t *total, *col_ptr;
+  Carve probe(nullptr);
+  carve(probe, &B, &R, &cnt, &total, &col_ptr, &crow, &cval, &norms_part, &cpart, &outp);
+  const size_t mark = probe.off;
+  carve_sketch(probe, m, d, zeta);
+  size_t need = probe.off;
+  probe.off = mark;
+  carve_factor(probe, ctx, d, n);
+  need = std::max(need, probe.off);
+  probe.off = mark;
+  PassGeom pg1{};
+  pg1.grid = 1;
+  carve_iter(probe, pg1, m, n);
+  need = std::max(need, probe.off);
+  if ((st = ensure_arena(ctx, need))) return st;
+  Carve cc(ctx->arena);
+  carve(cc, &B, &R, &cnt, &total, &col_ptr, &crow, &cval, &norms_part, &cpart, &outp);
+  const size_t mark2 = cc.off;
+  if ((st = reset_status(ctx))) return st;
+  const long long l0 = ctx->launches;
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+  {  // sketch: indices, CSR of S, sparse gather-add
+    SketchScratch sk = carve_sketch(cc, m, d, zeta);
+    CUDA_TRY(ctx, launch_sketch_indices(ctx, m, d, zeta, seed, sk.rows, sk.signs));
+    if ((st = sketch_csr_impl(ctx, m, d, zeta, sk.rows, sk.signs, sk.row_ptr, sk.ent, sk.fill))) return st;
+    CUDA_TRY(ctx, launch_sp_gather(ctx, d, sk.row_ptr, sk.ent, row_ptr, col, val, b, n,
+                                   1.0 / std::sqrt((double)zeta), B, d));
+  }
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+  cc.off = mark2;
+  double est[2];
+  if ((st = factor_impl(ctx, B, d, n, d, R, n, x, seed, cc, est))) return st;
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
+  cc.off = mark2;
+  // CSC copy of A for A^T r, then the iteration
+  CUDA_TRY(ctx, launch_sp_csc(ctx, m, n, row_ptr, col, val, cnt, total, col_ptr, crow, cval));
+  IterScratch s = carve_iter(cc, pg1, m, n);
+  CUDA_TRY(ctx, launch_prepare_R(ctx, R, n, n, nullptr, n, s.Rt, s.inv_diag));
+  IterState h{};
+  h.gamma = o.gamma; h.rho = o.rho; h.alpha = o.alpha; h.beta = o.beta;
+  h.normest = est[0]; h.condest = est[1];
+  IterState* hs = reinterpret_cast<IterState*>(reinterpret_cast<char*>(ctx->h_pinned) + 256);
+  *hs = h;
+  CUDA_TRY(ctx, cudaMemcpyAsync(s.st, hs, sizeof(IterState), cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(s.x_prev, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(s.r_prev, 0, sizeof(double) * m, ctx->stream));
+  StepArgs a{};
+  a.part = outp; a.nparts = 1; a.Rt = s.Rt; a.R = R; a.ldr = n; a.inv_diag = s.inv_diag; a.n = (int)n;
+  a.x = x; a.x_prev = s.x_prev; a.y = s.y; a.dvec = s.dvec; a.work = s.work; a.slots = s.slots; a.st = s.st;
+  a.use_stop = o.use_stop; a.extra = o.extra_iters; a.status = ctx->d_status;
+  IterState* hread = reinterpret_cast<IterState*>(reinterpret_cast<char*>(ctx->h_pinned) + 1024);
+  int launched = 0;
+  while (launched < q) {
+    const int k = std::min(8, q - launched);
+    for (int i = 0; i < k; ++i) {
+      CUDA_TRY(ctx, launch_sp_pass(ctx, m, n, row_ptr, col, val, b, x, s.r_prev, col_ptr, crow, cval, norms_part,
+                                   cpart, outp, s.st));
+      CUDA_TRY(ctx, launch_iter_step(ctx, a));
+    }
+    launched += k;
+    if (launched < q) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(hread, s.st, sizeof(IterState), cudaMemcpyDeviceToHost, ctx->stream));
+      CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      if (hread->done) break;
+    }
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(hread, s.st, sizeof(IterState), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], ctx->stream));
+  if ((st = sync_and_check(ctx))) return st;
+  if (info) {
+    std::memset(info, 0, sizeof *info);
+    info->iters = hread->iter;
+    info->res_norm = hread->rnorm;
+    info->step_norm = hread->dnorm;
+    info->normest = est[0];
+    info->condest = est[1];
+    info->stop_reason = hread->done ? (hread->nonfinite ? 3 : 0) : (o.use_stop ? 1 : 2);
+    cudaEventElapsedTime(&info->ms_sketch, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&info->ms_factor, ctx->ev[1], ctx->ev[2]);
+    cudaEventElapsedTime(&info->ms_iterate, ctx->ev[2], ctx->ev[3]);
+    info->launches = (int)(ctx->launches - l0);
+  }
+  if (hread->nonfinite) return fail(ctx, LS_ENONFINITE, "the iterate became non-finite");
+  if (!hread->done && o.use_stop) return LS_ENOTCONV;
+  return LS_OK;
+}
+
 ls_status ls_solve(ls_ctx* ctx, const double* A, const double* b, int64_t m, int64_t n, int64_t lda, int64_t d,
                    int zeta, int q, uint64_t seed, double* x, ls_info* info) {
   return ls_solve_ex(ctx, A, b, m, n, lda, d, zeta, q, seed, nullptr, x, info);

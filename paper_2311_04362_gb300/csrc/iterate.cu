@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constan
   double* xs = tiles + S * stage_doubles;
   double* rtile = xs + ((n + 1) & ~1);
   double* red = rtile + 2 * tr;                     // 2 * kConsumerWarps + 8
-  double* p1 = red + 2 * kConsumerWarps + 8;         // kConsumerWarps * 8 row-dot partials (n > 256)
-  uint64_t* full = reinterpret_cast<uint64_t*>(p1 + kConsumerWarps * 8);
+  double* p1 = red + 2 * kConsumerWarps + 8;         // kConsumerWarps * tr row-dot partials (n >= 32)
+  uint64_t* full = reinterpret_cast<uint64_t*>(p1 + kConsumerWarps * tr);
   uint64_t* empty = full + S;
   __shared__ int s_abort;
 
@@ -116,27 +116,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constan
     const int64_t row0 = (int64_t)t * tr;
     const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
 
-    if (nbox > 1) {
-      // phase 1 (n > 256, tr = 8 or 4): every warp takes all tr rows, LPR =
-      // 32 / tr lanes per row; lane (r, q) of warp w sums the columns
-      // c = LPR ((w + r) mod 8) + q (mod 8 LPR) -- each row's columns are
-      // covered once over the 8 warps, and the rotation by r puts the rows of
-      // a warp on different banks.  The LPR lanes are combined by shuffles,
-      // the 8 warps in warp order by one thread per row.  Per row this costs
-      // ~3.5 FP64 instructions besides the FMAs, against 9 for a warp per row
-      // (a 5-level shuffle tree and the row's scalar work on one lane).
-      const int LPR = 32 / tr, CS = 8 * LPR;
-      const int r = lane / LPR, q = lane - r * LPR;
+    if (n >= 32) {
+      // phase 1 (n >= 32): every warp takes all tr rows, in groups of RG = 8
+      // rows (4 when tr = 4) with LPR = 32 / RG lanes per row; lane (r, q) of
+      // warp w sums the columns c = LPR ((w + r) mod 8) + q (mod 8 LPR) --
+      // each row's columns are covered once over the 8 warps, and the
+      // rotation by r puts the rows of a warp on different banks.  The LPR
+      // lanes are combined by shuffles, the 8 warps in warp order by one
+      // thread per row.  Per row this costs ~3.5 FP64 instructions besides
+      // the FMAs, against 9 for a warp per row (a 5-level shuffle tree and the
+      // row's scalar work on one lane).
+      const int RG = tr < 8 ? tr : 8;
+      const int LPR = 32 / RG, CS = 8 * LPR;
+      const int rl = lane / LPR, q = lane - rl * LPR;
       double bj = 0.0, rpj = 0.0;
       if (tid < rows) {                       // issue the row's loads before the dots
         bj = a.b[row0 + tid];
         if (a.r_prev) rpj = a.r_prev[row0 + tid];
       }
-      double dot = 0.0;
-      if (r < rows)
-        for (int c = LPR * ((warp + r) & 7) + q; c < n; c += CS) dot += tl[tile_off(r, c, boxw, nbox, tr)] * xs[c];
-      for (int o = LPR >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-      if (q == 0) p1[warp * tr + r] = dot;
+      for (int r0 = 0; r0 < tr; r0 += RG) {
+        const int r = r0 + rl;
+        double dot = 0.0;
+        if (r < rows)
+          for (int c = LPR * ((warp + rl) & 7) + q; c < n; c += CS) dot += tl[tile_off(r, c, boxw, nbox, tr)] * xs[c];
+        for (int o = LPR >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        if (q == 0) p1[warp * tr + r] = dot;
+      }
       asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32));
       if (tid < tr) {
         double rj = 0.0;
@@ -351,7 +356,7 @@ PassGeom pass_geometry(const ls_ctx* ctx, int64_t n, int64_t m) {
   const int64_t ntiles = (m + g.tr - 1) / g.tr;
   g.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ntiles));
   g.smem = g.stages * stage + (size_t)((n + 1) & ~1LL) * 8 + 2 * g.tr * 8 + (2 * kConsumerWarps + 8) * 8 +
-           kConsumerWarps * 8 * 8 + 2 * g.stages * 8 + 128;
+           (size_t)kConsumerWarps * g.tr * 8 + 2 * g.stages * 8 + 128;
   // phase-2 group sums for n < 256 reuse the tile memory
   return g;
 }

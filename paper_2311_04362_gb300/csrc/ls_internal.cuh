@@ -353,6 +353,22 @@ struct StepArgs {
 };
 cudaError_t launch_iter_step(ls_ctx* ctx, const StepArgs& a);
 
+// sparse A (sparse.cu)
+size_t sp_gather_smem(int64_t n);
+cudaError_t launch_sp_gather(ls_ctx* ctx, int64_t d, const int64_t* srow, const uint32_t* sent, const int64_t* arp,
+                             const int32_t* acol, const double* aval, const double* b, int64_t n, double scale,
+                             double* B, int64_t ldb);
+int64_t sp_blocks(int64_t m);
+cudaError_t launch_sp_csc(ls_ctx* ctx, int64_t m, int64_t n, const int64_t* arp, const int32_t* acol,
+                          const double* aval, int32_t* cnt, int64_t* total, int64_t* col_ptr, int32_t* crow,
+                          double* cval);
+int sp_residual_grid(ls_ctx* ctx);
+int sp_segments(ls_ctx* ctx, int64_t n);
+cudaError_t launch_sp_pass(ls_ctx* ctx, int64_t m, int64_t n, const int64_t* arp, const int32_t* acol,
+                           const double* aval, const double* b, const double* x, double* r, const int64_t* col_ptr,
+                           const int32_t* crow, const double* cval, double* norms_part, double* cpart, double* out,
+                           const IterState* st);
+
 // batched path (batched.cu)
 // One problem of a batched solve or one server slot: caller's arrays, sizes,
 // offsets of its parts in the pools, and its pass tile geometry.

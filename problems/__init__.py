@@ -160,3 +160,38 @@ def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
     """Arrival times (seconds from 0) of a Poisson stream of the given rate."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, int(rate), 0xA77]))
     return np.cumsum(rng.exponential(1.0 / rate, count))
+
+
+# The sparse workload of Sec. 3.5: m = 3e6 rows with three nonzeros each in
+# uniformly random distinct columns, values +-1 uniformly, b standard
+# Gaussian, d = 30 n.
+SPARSE = dict(m=3_000_000, n=500, nnz_per_row=3, d_over_n=30, zeta=8, seed=0, q=100)
+
+
+def make_sparse(m: int, n: int, seed: int, nnz_per_row: int = 3):
+    """CSR (row_ptr int64, col int32 ascending within rows, val float64) and
+    b, numpy.  Distinct columns per row by the successive-shift method: the
+    k-th draw is uniform over n - k values and is shifted past the k smaller
+    columns already taken."""
+    assert nnz_per_row <= n
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5BA5E]))
+    cols = np.empty((m, nnz_per_row), dtype=np.int64)
+    for k in range(nnz_per_row):
+        c = rng.integers(0, n - k, m)
+        taken = np.sort(cols[:, :k], axis=1)
+        for t in range(k):
+            c = c + (c >= taken[:, t])
+        cols[:, k] = c
+    cols.sort(axis=1)
+    val = (rng.integers(0, 2, (m, nnz_per_row)) * 2 - 1).astype(np.float64)
+    b = rng.standard_normal(m)
+    row_ptr = np.arange(0, m * nnz_per_row + 1, nnz_per_row, dtype=np.int64)
+    return {"row_ptr": row_ptr, "col": cols.reshape(-1).astype(np.int32), "val": val.reshape(-1), "b": b,
+            "m": m, "n": n, "nnz": m * nnz_per_row}
+
+
+def sparse_to_dense(S):
+    A = np.zeros((S["m"], S["n"]))
+    rows = np.repeat(np.arange(S["m"]), np.diff(S["row_ptr"]))
+    A[rows, S["col"]] = S["val"]
+    return A

@@ -1,0 +1,102 @@
+"""GPU checks of the sparse-A path (ls_sketch_sparse, ls_solve_sparse) on the
+workload of Sec. 3.5: three nonzeros per row in random columns, values +-1,
+Gaussian b, d = 30 n.
+
+ * sketch: bit-identical to the oracle's sketch of the densified matrix (the
+   sparse gather is the dense left-to-right sum with its zero terms omitted);
+ * solution: within Wedin's bound of the oracle's Householder-QR solution:
+   both are backward stable, with a backward error that grows like sqrt(n) u
+   for these sizes (taken as eps = 10 sqrt(n) u), so they differ by at most
+   eps kappa (2 + kappa ||r|| / (||A|| ||x||));
+ * the same iterations as the dense path on the densified matrix, up to the
+   rounding floor of the stopping rule (max(5, iters / 4));
+ * determinism, and LS_ERANK for an empty column.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import problems
+from gpu_common import U, dev, host, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, ls = require_gpu()
+    ctx = ls.Context(0, torch.cuda.current_stream())
+    yield torch, ls, ctx
+    ctx.close()
+
+
+CASES = [(20000, 50, 1), (30000, 100, 2), (12000, 10, 3), (40000, 258, 4)]
+
+
+def _upload(torch, S):
+    return (dev(torch, S["row_ptr"]), dev(torch, S["col"]), dev(torch, S["val"]), dev(torch, S["b"]))
+
+
+@pytest.mark.parametrize("m,n,seed", CASES)
+def test_sparse_sketch_bit_identical(env, m, n, seed):
+    torch, ls, ctx = env
+    S = problems.make_sparse(m, n, seed)
+    rp, col, val, b = _upload(torch, S)
+    d = 30 * n
+    B = torch.empty(d * (n + 1), dtype=torch.float64, device="cuda")
+    ctx.ls_sketch_sparse(rp, col, val, m, n, b, d, 8, seed, B, d)
+    Bo = oracle.sketch(problems.sparse_to_dense(S), S["b"], d, 8, seed)
+    assert np.array_equal(host(B).reshape(n + 1, d).T, Bo)
+
+
+def _reference(S):
+    A = problems.sparse_to_dense(S)
+    x = oracle.qr_solve_lapack(A, S["b"]) if S["m"] * S["n"] ** 2 > 2e9 else oracle.qr_solve(A, S["b"])
+    r = S["b"] - A @ x
+    sv = np.linalg.svd(A, compute_uv=False)
+    kappa = sv[0] / sv[-1]
+    eps = 10 * np.sqrt(S["n"]) * U
+    bound = eps * kappa * (2 + kappa * np.linalg.norm(r) / (sv[0] * np.linalg.norm(x)))
+    return A, x, bound
+
+
+@pytest.mark.parametrize("m,n,seed", CASES)
+def test_sparse_solve_accuracy_and_dense_agreement(env, m, n, seed):
+    torch, ls, ctx = env
+    S = problems.make_sparse(m, n, seed)
+    rp, col, val, b = _upload(torch, S)
+    d = 30 * n
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    st, info = ctx.ls_solve_sparse(rp, col, val, m, n, S["nnz"], b, d, 8, 100, seed, x)
+    A, xq, bound = _reference(S)
+    err = np.linalg.norm(host(x) - xq) / np.linalg.norm(xq)
+    assert err <= bound, (err, bound)
+    # the dense path on the densified matrix: same sketch, same R, same start
+    xd = torch.empty(n, dtype=torch.float64, device="cuda")
+    std, infod = ctx.ls_solve(dev(torch, A), b, m, n, n, d, 8, 100, seed, xd)
+    assert info.normest == infod.normest and info.condest == infod.condest
+    assert abs(info.iters - infod.iters) <= max(5, infod.iters / 4), (info.iters, infod.iters)
+    assert np.linalg.norm(host(x) - host(xd)) / np.linalg.norm(host(xd)) <= bound
+
+
+def test_sparse_deterministic(env):
+    torch, ls, ctx = env
+    S = problems.make_sparse(30000, 100, 7)
+    rp, col, val, b = _upload(torch, S)
+    xs = []
+    for _ in range(2):
+        x = torch.empty(100, dtype=torch.float64, device="cuda")
+        ctx.ls_solve_sparse(rp, col, val, 30000, 100, S["nnz"], b, 3000, 8, 100, 0, x)
+        xs.append(host(x))
+    assert np.array_equal(xs[0], xs[1])
+
+
+def test_sparse_empty_column_is_rank_deficient(env):
+    torch, ls, ctx = env
+    S = problems.make_sparse(5000, 20, 8)
+    S["val"][S["col"] == 3] = 0.0
+    rp, col, val, b = _upload(torch, S)
+    x = torch.empty(20, dtype=torch.float64, device="cuda")
+    with pytest.raises(ls.LsError) as e:
+        ctx.ls_solve_sparse(rp, col, val, 5000, 20, S["nnz"], b, 600, 8, 100, 0, x)
+    assert e.value.status == ls.LS_ERANK
