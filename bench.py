@@ -395,7 +395,9 @@ def batched_case(ctx, stream, args, pg, world, rank):
     CUDA events on the launching stream.  Acceptance: the fraction of problems
     whose forward error is within 10x that of a Householder-QR solve (geqrf
     through torch) -- Algorithm 2 as stated and with the App. B momentum
-    weights (e = sqrt(n/d) = sqrt(1/20) for every problem)."""
+    weights (e = sqrt(n/d) = sqrt(1/20) for every problem).  The basic
+    method is timed with the default pass tiles and after ls_tune_batched
+    (whose time and table are reported); momentum with the tuned table."""
     import torch
 
     import paper_2311_04362_gb300 as ls
@@ -418,7 +420,13 @@ def batched_case(ctx, stream, args, pg, world, rank):
            "problems": nprob, "sum_m": int(sum(s["m"] for s in shapes)),
            "A_bytes": int(sum(8 * p["m"] * p["lda"] for p in probs))}
     steps = max(1, args.steps // 2)
-    for name, opts in (("basic", ls.default_opts()), ("momentum", ls.momentum_opts(1, 20))):
+    runs = [("basic_default_tiles", ls.default_opts(), False), ("basic", ls.default_opts(), True),
+            ("momentum", ls.momentum_opts(1, 20), True)]
+    for name, opts, tuned in runs:
+        if tuned and "tuning" not in out:
+            t0 = time.perf_counter()
+            report = ctx.ls_tune_batched(probs, reps=2)
+            out["tuning"] = {"seconds": time.perf_counter() - t0, "table": report.strip().splitlines()}
         ctx.ls_solve_batched(probs, cfg["zeta"], cfg["q"], opts)      # warm
         torch.cuda.synchronize()
         if pg:
@@ -441,6 +449,7 @@ def batched_case(ctx, stream, args, pg, world, rank):
                      "phase_ms": {"sketch": infos[0].ms_sketch, "factor": infos[0].ms_factor,
                                   "iterate": infos[0].ms_iterate},
                      "gpu_launches_per_batch": infos[0].launches}
+    ctx.ls_reset_tuning()
     del probs
     torch.cuda.empty_cache()
     return out

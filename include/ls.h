@@ -221,6 +221,24 @@ LS_API ls_status ls_solve_sparse(ls_ctx* ctx, const int64_t* row_ptr, const int3
                                  int64_t m, int64_t n, int64_t nnz, const double* b, int64_t d, int zeta, int q,
                                  uint64_t seed, const ls_opts* opts, double* x, ls_info* info);
 
+/* Autotuner of the batched pass (no counterpart in the paper; Sec. 3.3
+ * mentions tuning the implementation to the machine): for each class of n
+ * present in probs (n < 32, < 64, < 128, < 256, < 512, <= 1024), in turn,
+ * it times the fused pass on a sample of up to 64 problems of every class
+ * (x = 0, `reps` repetitions) for tile sizes {1536, 2560, 3840, 6144}
+ * doubles and {64, 128, 256} rows per work item, the other classes held
+ * fixed (the largest tile sets the launch's shared memory, so the classes
+ * interact), and keeps a choice that is at least 1% faster.  Later ls_solve_batched*
+ * calls and servers created from ctx use the table; the default is 3840 /
+ * 128 everywhere.  Reads A and b only.  A different table changes the order
+ * of the pass's sums, so results differ (within the same bounds) from an
+ * untuned run; with one table they are deterministic.  report (may be NULL)
+ * receives one line per class and the sample's pass time before and after.
+ * ls_reset_tuning restores the defaults. */
+LS_API ls_status ls_tune_batched(ls_ctx* ctx, const ls_problem* probs, int nprob, int reps, char* report,
+                                 size_t report_len);
+LS_API ls_status ls_reset_tuning(ls_ctx* ctx);
+
 /* Mixed precision (no counterpart in the paper's experiments; Sec. 3.2 reads
  * the iteration as iterative refinement, which tolerates a preconditioner R
  * perturbed by c kappa u32): as ls_solve_batched, but the sketch is summed in

@@ -100,6 +100,10 @@ def lib():
     L.ls_solve_batched.restype = S
     L.ls_solve_batched_mixed.argtypes = [P, C.POINTER(ls_problem), I, I, I, C.POINTER(ls_opts), C.POINTER(ls_info)]
     L.ls_solve_batched_mixed.restype = S
+    L.ls_tune_batched.argtypes = [P, C.POINTER(ls_problem), I, I, C.c_char_p, C.c_size_t]
+    L.ls_tune_batched.restype = S
+    L.ls_reset_tuning.argtypes = [P]
+    L.ls_reset_tuning.restype = S
     L.ls_sketch_sparse.argtypes = [P, P, P, P, I64, I64, P, I64, I, C.c_uint64, P, I64]
     L.ls_sketch_sparse.restype = S
     L.ls_solve_sparse.argtypes = [P, P, P, P, I64, I64, I64, P, I64, I, I, C.c_uint64, C.POINTER(ls_opts), P,
@@ -269,6 +273,19 @@ class Context:
         fn = lib().ls_solve_batched_mixed if mixed else lib().ls_solve_batched
         self._check(fn(self._h, arr, len(probs), zeta, q, C.byref(opts) if opts is not None else None, infos))
         return infos
+
+    def ls_tune_batched(self, probs, reps=3) -> str:
+        arr = (ls_problem * len(probs))()
+        for i, p in enumerate(probs):
+            arr[i] = p if isinstance(p, ls_problem) else ls_problem(
+                _ptr(p["A"]), _ptr(p["b"]), _ptr(p.get("x")), p["m"], p["n"], p["lda"], p["d"], p.get("seed", i),
+                None, None)
+        buf = C.create_string_buffer(4096)
+        self._check(lib().ls_tune_batched(self._h, arr, len(probs), reps, buf, 4096))
+        return buf.value.decode()
+
+    def ls_reset_tuning(self):
+        return self._check(lib().ls_reset_tuning(self._h))
 
     def ls_solve_batched_mixed(self, probs, zeta, q, opts=None, infos=None):
         return self.ls_solve_batched(probs, zeta, q, opts, infos, mixed=True)

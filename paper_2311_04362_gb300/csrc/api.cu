@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include <string>
 #include <vector>
 
 #include "ls_internal.cuh"
@@ -614,7 +615,7 @@ static ls_status solve_batched_impl(ls_ctx* ctx, const ls_problem* probs, int np
   std::vector<char> hP(bprob_bytes() * (size_t)np);
   BProb* hp = reinterpret_cast<BProb*>(hP.data());
   BatchPlan pl;
-  batch_plan(probs, np, hp, pl);
+  batch_plan(probs, np, hp, pl, ctx->tune);
   std::vector<int64_t> hoffs(3 * (size_t)np);
   batch_offsets(hp, np, hoffs.data(), hoffs.data() + np, hoffs.data() + 2 * np);
   std::vector<int> horder((size_t)np);
@@ -729,7 +730,7 @@ static ls_status solve_batched_impl(ls_ctx* ctx, const ls_problem* probs, int np
   CUDA_TRY(ctx, launch_b_compact(ctx, dP, np, pools, alist, aoff, cnt));
   int64_t* hcnt = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(ctx->h_pinned) + 2048);
   for (int i = 0; i < q; ++i) {
-    CUDA_TRY(ctx, launch_b_pass(ctx, dP, alist, aoff, cnt, pl.max_n, pl.ttotal, pools));
+    CUDA_TRY(ctx, launch_b_pass(ctx, dP, alist, aoff, cnt, pl.max_n, pl.cap, pl.ttotal, pools));
     CUDA_TRY(ctx, launch_b_step(ctx, dP, alist, cnt, np, pools, o.use_stop, o.extra_iters, q));
     CUDA_TRY(ctx, launch_b_compact(ctx, dP, np, pools, alist, aoff, cnt));
     if ((i & 7) == 7 && i + 1 < q) {
@@ -771,6 +772,122 @@ extern "C" {
 ls_status ls_solve_batched(ls_ctx* ctx, const ls_problem* probs, int np, int zeta, int q, const ls_opts* opts,
                            ls_info* infos) {
   return solve_batched_impl(ctx, probs, np, zeta, q, opts, infos, false);
+}
+
+// Time `reps` passes (after one warm-up) over the problems `sub` with pass
+// table t; *ms = the average.  The pass reads A and b and writes only
+// scratch (x = 0 of its own).
+static ls_status time_pass(ls_ctx* ctx, const std::vector<ls_problem>& sub, const PassTune& t, int reps, float* ms) {
+  const int ns = (int)sub.size();
+  std::vector<char> hP(bprob_bytes() * (size_t)ns);
+  BProb* hp = reinterpret_cast<BProb*>(hP.data());
+  BatchPlan pl;
+  batch_plan(sub.data(), ns, hp, pl, t);
+  auto carve_t = [&](Carve& c, BProb** dP, BPools* pools, double** xs, int** alist, int64_t** aoff, int64_t** cnt) {
+    *dP = reinterpret_cast<BProb*>(c.take<char>(bprob_bytes() * (size_t)ns));
+    *pools = BPools{};
+    pools->part = c.take<double>((size_t)pl.ptotal);
+    pools->r_prev = c.take<double>((size_t)pl.mtotal);
+    pools->st = c.take<IterState>((size_t)ns);
+    *xs = c.take<double>((size_t)pl.vtotal);
+    *alist = c.take<int>((size_t)ns);
+    *aoff = c.take<int64_t>((size_t)ns);
+    *cnt = c.take<int64_t>(4);
+  };
+  BProb* dP; BPools pools; double* xs; int* alist; int64_t* aoff; int64_t* cnt;
+  Carve probe(nullptr);
+  carve_t(probe, &dP, &pools, &xs, &alist, &aoff, &cnt);
+  ls_status st;
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  carve_t(cc, &dP, &pools, &xs, &alist, &aoff, &cnt);
+  int64_t xo = 0;
+  for (int i = 0; i < ns; ++i) {
+    hp[i].x = xs + xo;
+    xo += hp[i].n;
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(dP, hp, bprob_bytes() * (size_t)ns, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(xs, 0, sizeof(double) * (size_t)pl.vtotal, ctx->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(pools.r_prev, 0, sizeof(double) * (size_t)pl.mtotal, ctx->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(pools.st, 0, sizeof(IterState) * (size_t)ns, ctx->stream));
+  CUDA_TRY(ctx, launch_b_compact(ctx, dP, ns, pools, alist, aoff, cnt));
+  CUDA_TRY(ctx, launch_b_pass(ctx, dP, alist, aoff, cnt, pl.max_n, pl.cap, pl.ttotal, pools));   // warm
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+  for (int r = 0; r < reps; ++r) {
+    CUDA_TRY(ctx, launch_b_compact(ctx, dP, ns, pools, alist, aoff, cnt));
+    CUDA_TRY(ctx, launch_b_pass(ctx, dP, alist, aoff, cnt, pl.max_n, pl.cap, pl.ttotal, pools));
+  }
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+  if ((st = sync_and_check(ctx))) return st;
+  float t_ms = 0.0f;
+  cudaEventElapsedTime(&t_ms, ctx->ev[0], ctx->ev[1]);
+  *ms = t_ms / (float)reps;
+  return LS_OK;
+}
+
+ls_status ls_tune_batched(ls_ctx* ctx, const ls_problem* probs, int np, int reps, char* report, size_t report_len) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  if (np < 1 || !probs) return fail(ctx, LS_EINVAL, "invalid problem array");
+  if (reps < 1) reps = 3;
+  for (int p = 0; p < np; ++p) {
+    ls_status st;
+    if (!probs[p].b) return fail(ctx, LS_EINVAL, "problem %d: null b", p);
+    if ((st = check_A(ctx, probs[p].A, probs[p].m, probs[p].n, probs[p].lda))) return st;
+    if (probs[p].n > 1024) return fail(ctx, LS_EINVAL, "problem %d: n above 1024", p);
+  }
+  cudaSetDevice(ctx->device);
+  // a sample with up to 64 problems of every class present: the launch-wide
+  // buffer size couples the classes, so candidates are timed on the mix
+  std::vector<int> per(kTuneBuckets, 0);
+  std::vector<ls_problem> sub;
+  for (int p = 0; p < np; ++p) {
+    const int b = tune_bucket(probs[p].n);
+    if (per[b] < 64) { sub.push_back(probs[p]); ++per[b]; }
+  }
+  static const int kTiles[] = {1536, 2560, 3840, 6144};
+  static const int kItems[] = {64, 128, 256};
+  PassTune table = ctx->tune;
+  float best = 0.0f;
+  ls_status st;
+  if ((st = time_pass(ctx, sub, table, reps, &best))) return st;
+  const float start = best;
+  std::string rep;
+  // one sweep of coordinate descent over the classes present
+  for (int bkt = 0; bkt < kTuneBuckets; ++bkt) {
+    if (per[bkt] == 0) continue;
+    for (int tile : kTiles) {
+      for (int items : kItems) {
+        if (tile == table.tile[bkt] && items == table.item_rows[bkt]) continue;
+        PassTune t = table;
+        t.tile[bkt] = tile;
+        t.item_rows[bkt] = items;
+        float ms = 0.0f;
+        if ((st = time_pass(ctx, sub, t, reps, &ms))) return st;
+        if (ms < 0.99f * best) { best = ms; table = t; }
+      }
+    }
+    table.tuned[bkt] = 1;
+    char line[160];
+    snprintf(line, sizeof line, "n<%d: tile %d doubles, %d rows per item\n", 32 << bkt, table.tile[bkt],
+             table.item_rows[bkt]);
+    rep += line;
+  }
+  char tail[160];
+  snprintf(tail, sizeof tail, "pass over the %d-problem sample: %.3f ms -> %.3f ms\n", (int)sub.size(), start, best);
+  rep += tail;
+  ctx->tune = table;
+  if (report && report_len) {
+    std::strncpy(report, rep.c_str(), report_len - 1);
+    report[report_len - 1] = 0;
+  }
+  return LS_OK;
+}
+
+ls_status ls_reset_tuning(ls_ctx* ctx) {
+  if (!ctx) return LS_EINVAL;
+  ctx->tune = default_tune();
+  return LS_OK;
 }
 
 ls_status ls_solve_batched_mixed(ls_ctx* ctx, const ls_problem* probs, int np, int zeta, int q, const ls_opts* opts,

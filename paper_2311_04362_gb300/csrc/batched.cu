@@ -862,8 +862,8 @@ __global__ void k_b_iter_init(const BProb* __restrict__ P, const int* __restrict
 }
 
 static constexpr int kBThreads = 256;
-static constexpr int kBTileCap = 3840;      // doubles per tile buffer (30 KB): 3 CTAs per SM
-static constexpr int kBItemRows = 128;      // rows per pass item (one partial per item)
+// The tile size and rows per item come from the PassTune table (defaults:
+// 3840 doubles, i.e. 30 KB per buffer and 3 CTAs per SM; 128 rows per item).
 
 // Active problems in index order (alist) and the exclusive prefix of their
 // pass items (aoff); cnt[0] = active problems, cnt[1] = their items, cnt[2] =
@@ -953,10 +953,10 @@ __device__ inline BItem b_locate(const int* __restrict__ alist, const int64_t* _
 __global__ void __launch_bounds__(kBThreads, 3) k_b_pass(const BProb* __restrict__ P, const int* __restrict__ alist,
                                                          const int64_t* __restrict__ aoff,
                                                          int64_t* __restrict__ cnt, BPools pl, int max_n,
-                                                         unsigned int* __restrict__ status) {
+                                                         int cap, unsigned int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* buf0 = reinterpret_cast<double*>(smem_raw);
-  double* xs = buf0 + 2 * kBTileCap;                 // max_n (even)
+  double* xs = buf0 + 2 * (size_t)cap;               // max_n (even)
   double* part1 = xs + ((max_n + 1) & ~1);           // 256
   double* rt = part1 + kBThreads;                    // 256
   double* q1 = rt + kBThreads;                       // 256: r_j
@@ -999,7 +999,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_b_pass(const BProb* __restrict
     for (int t = t0; t < t1; ++t, ++k) {
       // prefetch the next tile of this item, else the first tile of the next item
       if (warp == 0) {
-        double* nb = buf0 + (size_t)((k + 1) & 1) * kBTileCap;
+        double* nb = buf0 + (size_t)((k + 1) & 1) * cap;
         if (t + 1 < t1) b_issue_tile(pr, t + 1, nb, &bar[(k + 1) & 1], lane);
         else if (nxt.v >= 0) {
           const BProb& pn = P[nxt.p];
@@ -1007,7 +1007,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_b_pass(const BProb* __restrict
         }
       }
       const bool more = (t + 1 < t1) || (nxt.v >= 0);
-      const double* tl = buf0 + (size_t)(k & 1) * kBTileCap;
+      const double* tl = buf0 + (size_t)(k & 1) * cap;
       const int64_t row0 = (int64_t)t * TR;
       const int rows = (int)min((int64_t)TR, pr.m - row0);
       const bool ok = mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1, gtimer() + LS_WAIT_NS);
@@ -1200,20 +1200,27 @@ __global__ void __launch_bounds__(256) k_b_step(const BProb* __restrict__ P, con
 // Pass tile of a problem: shared-memory row stride ss = 2 mod 4 doubles (at
 // most 2-way bank conflicts when threads read down a column), rows per tile
 // tr = min(256, cap / ss), and S = 256 / tr column chunks per row dot.
-static void pass_tile(int64_t n, int64_t lda, BProb& b) {
+static void pass_tile(int64_t n, int64_t lda, int tile, BProb& b) {
   const int ss = (int)((lda % 4 == 2) ? lda : lda + 2);
   b.ss = ss;
   b.rowcopy = (ss != lda) ? 1 : 0;
-  b.tr = std::max(1, std::min(256, kBTileCap / ss));
+  b.tr = std::max(1, std::min(256, tile / ss));
   b.S = std::max(1, 256 / b.tr);
   (void)n;
 }
 
-void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl) {
+int tune_cap(const PassTune& t) {
+  int c = 0;
+  for (int b = 0; b < kTuneBuckets; ++b) c = std::max(c, t.tile[b]);
+  return c;
+}
+
+void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl, const PassTune& tune) {
   pl.np = np;
   pl.mtotal = pl.dtotal = pl.btotal = pl.rtotal = pl.vtotal = pl.ttotal = pl.ptotal = pl.wtotal = 0;
   pl.max_d = 0;
   pl.max_m = 0;
+  pl.cap = 0;
   pl.max_fill = 0.0;
   pl.max_n = 0;
   pl.max_tile_doubles = 0;
@@ -1224,10 +1231,12 @@ void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl) {
     b.moff = pl.mtotal; b.doff = pl.dtotal; b.boff = pl.btotal; b.roff = pl.rtotal; b.voff = pl.vtotal;
     b.rpoff = pl.mtotal;
     b.toff = pl.wtotal; b.poff = pl.ptotal;
-    pass_tile(q.n, q.lda, b);
+    const int tb = tune_bucket(q.n);
+    pass_tile(q.n, q.lda, tune.tile[tb], b);
     b.gw = (q.n + 1 > 16) ? 32 : (q.n + 1 > 8) ? 16 : (q.n + 1 > 4) ? 8 : 4;
     b.tiles = (int)((q.m + b.tr - 1) / b.tr);
-    b.tpi = std::max(1, (kBItemRows + b.tr - 1) / b.tr);
+    b.tpi = std::max(1, (tune.item_rows[tb] + b.tr - 1) / b.tr);
+    pl.cap = std::max(pl.cap, b.tr * b.ss);
     b.items = (b.tiles + b.tpi - 1) / b.tpi;
     pl.mtotal += q.m; pl.dtotal += q.d; pl.btotal += q.d * (q.n + 1); pl.rtotal += 2 * q.n * q.n;
     pl.vtotal += V_COUNT * q.n; pl.ttotal += b.items; pl.ptotal += (int64_t)b.items * (q.n + 2);
@@ -1452,14 +1461,14 @@ cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, int np, const BPools&
   return cudaGetLastError();
 }
 
-size_t b_pass_smem(int max_n) {
-  return sizeof(double) * (2 * (size_t)kBTileCap + (size_t)((max_n + 1) & ~1) + 5 * kBThreads) + 2 * sizeof(uint64_t);
+size_t b_pass_smem(int max_n, int cap) {
+  return sizeof(double) * (2 * (size_t)cap + (size_t)((max_n + 1) & ~1) + 5 * kBThreads) + 2 * sizeof(uint64_t);
 }
 
 // Grid of the persistent pass for problems of up to max_n columns (also
 // sets the kernel's shared-memory limit; call before capturing a launch).
-int b_pass_grid(ls_ctx* ctx, int max_n) {
-  const size_t smem = b_pass_smem(max_n);
+int b_pass_grid(ls_ctx* ctx, int max_n, int cap) {
+  const size_t smem = b_pass_smem(max_n, cap);
   if (cudaFuncSetAttribute(k_b_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_pass, kBThreads, smem);
@@ -1467,12 +1476,12 @@ int b_pass_grid(ls_ctx* ctx, int max_n) {
 }
 
 cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* aoff, int64_t* cnt,
-                          int max_n, int64_t max_items, const BPools& pools) {
-  const size_t smem = b_pass_smem(max_n);
-  const int g = b_pass_grid(ctx, max_n);
+                          int max_n, int cap, int64_t max_items, const BPools& pools) {
+  const size_t smem = b_pass_smem(max_n, cap);
+  const int g = b_pass_grid(ctx, max_n, cap);
   if (g == 0) return cudaErrorInvalidValue;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(max_items, (int64_t)g));
-  k_b_pass<<<(unsigned)grid, kBThreads, smem, ctx->stream>>>(dP, alist, aoff, cnt, pools, max_n, ctx->d_status);
+  k_b_pass<<<(unsigned)grid, kBThreads, smem, ctx->stream>>>(dP, alist, aoff, cnt, pools, max_n, cap, ctx->d_status);
   ++ctx->launches;
   return cudaGetLastError();
 }

@@ -248,6 +248,24 @@ __device__ inline float warp_sum(float v) {
 }  // namespace lsk
 
 // -------------------------------------------------------------------- context
+// Geometry of the batched fused pass, per class of n (the autotuner's table).
+constexpr int kTuneBuckets = 6;   // n in [1,32), [32,64), [64,128), [128,256), [256,512), [512,1024]
+struct PassTune {
+  int tile[kTuneBuckets];       // doubles of one tile (tr * stride <= tile)
+  int item_rows[kTuneBuckets];  // rows per pass item (one partial per item)
+  int tuned[kTuneBuckets];      // 1 where a measurement chose the entry
+};
+inline int tune_bucket(int64_t n) {
+  int b = 0;
+  while (b < kTuneBuckets - 1 && n >= (32ll << b)) ++b;
+  return b;
+}
+inline PassTune default_tune() {
+  PassTune t;
+  for (int b = 0; b < kTuneBuckets; ++b) { t.tile[b] = 3840; t.item_rows[b] = 128; t.tuned[b] = 0; }
+  return t;
+}
+
 struct ls_ctx {
   int device = 0;
   int num_sms = 0;
@@ -275,6 +293,8 @@ struct ls_ctx {
   int cluster = 8;
   // TMA encode entry point
   void* encode_tiled = nullptr;
+  // batched pass geometry (ls_tune_batched)
+  PassTune tune = default_tune();
 };
 
 // ------------------------------------------------------------ launch helpers
@@ -417,6 +437,7 @@ struct BatchPlan {
   int64_t wtotal;                // gather warps
   int max_n, max_tile_doubles;   // max_tile_doubles: unused
   int64_t max_d, max_m;
+  int cap;                       // doubles per pass buffer (largest tile used)
   double max_fill;               // largest m / d (mean bucket size / zeta)
 };
 bool b_csr_fits(const BatchPlan& pl);
@@ -424,7 +445,8 @@ int64_t b_csr_global_entries();
 cudaError_t launch_b_csr(ls_ctx* ctx, const BProb* dP, const BatchPlan& pl, int zeta, const int32_t* rows,
                          const uint32_t* signs, int64_t* row_ptr, uint32_t* ent, uint32_t* scratch);
 size_t bprob_bytes();
-void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl);
+void batch_plan(const ls_problem* probs, int np, BProb* out, BatchPlan& pl, const PassTune& tune);
+int tune_cap(const PassTune& t);   // the largest tile of the table (doubles per pass buffer)
 void batch_offsets(const BProb* P, int np, int64_t* moffs, int64_t* doffs, int64_t* toffs);
 int64_t batch_boff(const BProb* P, int p);
 int64_t batch_roff(const BProb* P, int p);
@@ -448,9 +470,9 @@ cudaError_t launch_b_iter_init(ls_ctx* ctx, const BProb* dP, int count, const in
                                double gamma, double rho, double alpha, double beta);
 cudaError_t launch_b_compact(ls_ctx* ctx, const BProb* dP, int np, const BPools& pools, int* alist, int64_t* aoff,
                              int64_t* cnt);
-int b_pass_grid(ls_ctx* ctx, int max_n);
+int b_pass_grid(ls_ctx* ctx, int max_n, int cap);
 cudaError_t launch_b_pass(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* aoff, int64_t* cnt,
-                          int max_n, int64_t max_items, const BPools& pools);
+                          int max_n, int cap, int64_t max_items, const BPools& pools);
 cudaError_t launch_b_step(ls_ctx* ctx, const BProb* dP, const int* alist, const int64_t* cnt, int np,
                           const BPools& pools, int use_stop, int extra, int q);
 cudaError_t launch_correct(ls_ctx* ctx, const StepArgs& a);

@@ -176,7 +176,9 @@ struct ls_server {
   int inflight = 0;
   cudaGraphExec_t graph = nullptr;
   int pass_grid = 0;
+  int pass_cap = 0;             // doubles per pass buffer
   int qr_csize = 0;             // CTAs per cluster of the large-problem QR (0: not used)
+  PassTune tune = default_tune();  // pass geometry, copied from the creating context
   BDone* h_rec = nullptr;      // pinned
   unsigned int* h_count = nullptr;
   // pinned staging of one admission batch (read by its async copies)
@@ -221,7 +223,7 @@ ls_status capture_step(ls_server* s) {
   SRV_CUDA(s, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = launch_b_compact(ctx, s->dslots, s->cap, s->pools, s->alist, s->aoff, s->cnt);
   if (e == cudaSuccess)
-    e = launch_b_pass(ctx, s->dslots, s->alist, s->aoff, s->cnt, s->max_n, (int64_t)1 << 40, s->pools);
+    e = launch_b_pass(ctx, s->dslots, s->alist, s->aoff, s->cnt, s->max_n, s->pass_cap, (int64_t)1 << 40, s->pools);
   if (e == cudaSuccess)
     e = launch_b_step(ctx, s->dslots, s->alist, s->cnt, s->cap, s->pools, s->opts.use_stop, s->opts.extra_iters, s->q);
   cudaGraph_t g = nullptr;
@@ -247,7 +249,7 @@ ls_status admit(ls_server* s, int* kout) {
     const ls_server::Req& r = s->queue.front();
     BProb tmp;
     BatchPlan one;
-    batch_plan(&r.p, 1, &tmp, one);
+    batch_plan(&r.p, 1, &tmp, one, s->tune);
     const Layout L = request_layout(r.p.m, r.p.n, r.p.d, tmp.items);
     const size_t admit = L.total + resident_bytes(r.p);
     if (s->admit_used + admit > s->admit_budget) break;
@@ -278,7 +280,7 @@ ls_status admit(ls_server* s, int* kout) {
   if (k == 0) return LS_OK;
   // admission batch: sketch offsets local to the batch, B in the slots' regions
   BatchPlan pl;
-  batch_plan(ps.data(), k, s->h_adm, pl);
+  batch_plan(ps.data(), k, s->h_adm, pl, s->tune);
   for (int i = 0; i < k; ++i) s->h_adm[i].boff = s->h_slots[slots[i]].boff;
   batch_offsets(s->h_adm, k, s->h_offs, s->h_offs + k, s->h_offs + 2 * k);
   std::vector<int> order(k);
@@ -376,7 +378,7 @@ size_t ls_server_request_bytes(int64_t m, int64_t n, int64_t lda, int64_t d) {
   p.m = m; p.n = n; p.lda = lda; p.d = d;
   BProb tmp;
   BatchPlan one;
-  batch_plan(&p, 1, &tmp, one);
+  batch_plan(&p, 1, &tmp, one, default_tune());
   return request_layout(m, n, d, tmp.items).total + resident_bytes(p);
 }
 
@@ -453,7 +455,9 @@ ls_status ls_server_create(ls_ctx* user, int max_inflight, int64_t max_n, size_t
   k_srv_init_states<<<(cap + 255) / 256, 256, 0, s->ctx->stream>>>(s->pools.st, s->pools.pstatus, cap);
   s->live.assign(cap, ls_server::Live());
   for (int i = cap - 1; i >= 0; --i) s->free_slots.push_back(i);
-  s->pass_grid = b_pass_grid(s->ctx, s->max_n);
+  s->tune = user->tune;
+  s->pass_cap = std::max(tune_cap(s->tune), s->max_n + 4);   // every slot's tile fits
+  s->pass_grid = b_pass_grid(s->ctx, s->max_n, s->pass_cap);
   s->qr_csize = b_qr_cluster_size(s->ctx);
   if (s->pass_grid == 0) return bad("pass configuration");
   if (cudaStreamSynchronize(s->ctx->stream) != cudaSuccess) return bad("server set-up");
@@ -499,7 +503,7 @@ ls_status ls_server_submit(ls_server* s, const ls_problem* p, int64_t* ticket) {
   const size_t need = ls_server_request_bytes(p->m, p->n, p->lda, p->d);
   BProb tmp;
   BatchPlan one;
-  batch_plan(p, 1, &tmp, one);
+  batch_plan(p, 1, &tmp, one, s->tune);
   if (need > s->admit_budget || request_layout(p->m, p->n, p->d, tmp.items).total > s->arena_bytes)
     return srv_fail(s, LS_ENOMEM, "request larger than the server's budget");
   ls_server::Req r;
