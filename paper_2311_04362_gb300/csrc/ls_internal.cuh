@@ -295,6 +295,10 @@ struct ls_ctx {
   void* encode_tiled = nullptr;
   // batched pass geometry (ls_tune_batched)
   PassTune tune = default_tune();
+  // host inputs of ls_solve*: A is uploaded on a stream of its own while the
+  // sketch's indices and CSR (which do not read A) run on `stream`
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_done = nullptr;
 };
 
 // ------------------------------------------------------------ launch helpers
