@@ -62,3 +62,47 @@ def test_damping_and_momentum_weights(libpath):
     o = ls.momentum_opts(n, d)
     assert o.alpha == pytest.approx((1 - e2) ** 2, rel=1e-15) and o.beta == pytest.approx(e2, rel=1e-15)
     assert o.use_stop == 1 and o.rho == 0.04
+
+
+def test_header_declares_the_next_rows():
+    syms = declared_symbols()
+    for s in ["ls_solve_batched", "ls_solve_batched_mixed", "ls_tune_batched", "ls_reset_tuning", "ls_server_create",
+              "ls_server_submit", "ls_server_step", "ls_server_poll", "ls_server_get_stats", "ls_server_destroy",
+              "ls_server_request_bytes", "ls_sketch_sparse", "ls_solve_sparse", "ls_opts_damping",
+              "ls_opts_momentum", "ls_residual_gradient_noalloc"]:
+        assert s in syms, s
+
+
+def test_server_request_bytes_accounting(libpath):
+    """Host-only: a request counts its resident A, b, x plus the workspace
+    (sketch d (n+1), R and R^T 2 n^2, eight n-vectors, pass partials, r_prev),
+    each rounded up to 256 bytes."""
+    import paper_2311_04362_gb300 as ls
+
+    def al(x):
+        return (x + 255) // 256 * 256
+
+    for m, n, lda, d in [(1000, 10, 10, 200), (50000, 123, 124, 2460), (500000, 500, 500, 10000)]:
+        got = ls.server_request_bytes(m, n, lda, d)
+        resident = al(8 * m * lda) + al(8 * m) + al(8 * n)
+        fixed = al(8 * d * (n + 1)) + al(16 * n * n) + al(64 * n) + al(8 * m)
+        assert got > resident + fixed                       # plus the pass partials
+        partials = got - resident - fixed
+        assert 0 < partials <= al(8 * (n + 2) * m)          # at most one partial per row
+    assert ls.server_request_bytes(0, 10, 10, 200) == 0
+    assert ls.server_request_bytes(100, 10, 8, 200) == 0    # lda < n
+    assert ls.server_request_bytes(2000, 20, 20, 400) < ls.server_request_bytes(4000, 20, 20, 400)
+    assert ls.server_request_bytes(4000, 20, 20, 400) < ls.server_request_bytes(4000, 40, 40, 800)
+
+
+def test_api_rejects_without_a_context(libpath):
+    """Host-only argument checks: a null context is LS_EINVAL everywhere."""
+    import ctypes as C
+    import paper_2311_04362_gb300 as ls
+    L = ls.lib()
+    assert L.ls_solve_batched(None, None, 0, 8, 100, None, None) == ls.LS_EINVAL
+    assert L.ls_tune_batched(None, None, 0, 1, None, 0) == ls.LS_EINVAL
+    assert L.ls_server_destroy(None) == ls.LS_EINVAL
+    assert L.ls_solve_sparse(None, None, None, None, 10, 2, 20, None, 4, 8, 10, 0, None, None, None) == ls.LS_EINVAL
+    n_out = C.c_int()
+    assert L.ls_server_poll(None, None, None, 0, C.byref(n_out)) == ls.LS_EINVAL
