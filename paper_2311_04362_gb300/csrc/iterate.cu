@@ -35,6 +35,19 @@ struct PassArgs {
   unsigned int* status;
 };
 
+// OR of v over the `nthreads` threads (a multiple of 32) that meet at named
+// barrier `id`: a group-uniform decision (e.g. to leave a loop after a
+// bounded wait gave up) so that no warp is left at a later named barrier.
+__device__ inline bool bar_any(bool v, int id, int nthreads) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
 // Shared-memory offset (in doubles) of element (row r, column c) of a tile.
 __device__ inline int tile_off(int r, int c, int boxw, int nbox, int tr) {
   return (nbox == 1) ? (r * boxw + c) : ((c >> 8) * (tr * 256) + r * 256 + (c & 255));
@@ -107,8 +120,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constan
   int k = 0;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
     const int s = k % S;
-    if (!mbar_wait_bounded(&full[s], (k / S) & 1, deadline)) {
-      atomicOr(a.status, LS_DEV_TIMEOUT);
+    const bool ok = mbar_wait_bounded(&full[s], (k / S) & 1, deadline);
+    if (bar_any(!ok, 1, kConsumerWarps * 32)) {        // every consumer warp leaves together
+      if (!ok) atomicOr(a.status, LS_DEV_TIMEOUT);
       break;
     }
     const double* tl = tiles + (size_t)s * stage_doubles;
@@ -231,6 +245,170 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constan
     out[n + 1] = s2;
   }
   (void)s_abort;
+}
+
+// k_fused_pass_ws: the same pass for n > 256 (tr = 8 or 4), warp-specialized
+// so that the FP64 pipe does not idle at block-wide barriers between the two
+// uses of a tile.  Warps 0-3 (row group) form the row dots of tile k -- lane
+// (r, q) of warp w sums the columns c = LPR ((w + r) mod 4) + q (mod 4 LPR),
+// LPR = 32 / tr -- combine them (two shuffles, then the 4 warps in warp order
+// by one thread per row), form r_j and the norms, and hand r to the column
+// group through an mbarrier; warps 4-7 (column group) add r_j A_jk to their
+// columns for tile k while the row group is already on tile k + 1.  The r
+// buffer and the row-dot partials are double-buffered; the column group
+// releases a tile's stage and its r buffer.  Same arithmetic as the phases of
+// k_fused_pass (and the same deterministic orders within a CTA).
+template <int NPT2>
+__global__ void __launch_bounds__(kThreads, 1) k_fused_pass_ws(const __grid_constant__ CUtensorMap map, PassArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (a.st && a.st->done) return;
+  constexpr int kRW = kConsumerWarps / 2;          // row-group warps (the rest: column group)
+  const int n = a.n, tr = a.tr, boxw = a.boxw, nbox = a.nbox, S = a.stages;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  const size_t stage_doubles = (size_t)tr * nbox * boxw;
+  double* tiles = reinterpret_cast<double*>(smem_raw);
+  double* xs = tiles + S * stage_doubles;
+  double* rtile = xs + ((n + 1) & ~1);              // [2][tr]
+  double* red = rtile + 2 * tr;
+  double* p1 = red + 2 * kConsumerWarps + 8;        // [2][kRW][tr] row-dot partials
+  uint64_t* full = reinterpret_cast<uint64_t*>(p1 + kConsumerWarps * tr);
+  uint64_t* empty = full + S;
+  uint64_t* rready = empty + S;                     // [2] r of a tile written
+  uint64_t* rfree = rready + 2;                     // [2] r of a tile consumed
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], kConsumerWarps - kRW); }
+    for (int i = 0; i < 2; ++i) { mbar_init(&rready[i], 1); mbar_init(&rfree[i], kConsumerWarps - kRW); }
+    fence_mbar_init();
+  }
+  for (int i = tid; i < n; i += blockDim.x) xs[i] = a.x[i];
+  __syncthreads();
+  const uint32_t tile_bytes = (uint32_t)(stage_doubles * sizeof(double));
+  double* out = a.part + (size_t)blockIdx.x * (n + 2);
+
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      prefetch_tmap(&map);
+      int k = 0;
+      for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+        const int s = k % S;
+        if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1, gtimer() + LS_WAIT_NS)) {
+          atomicOr(a.status, LS_DEV_TIMEOUT);
+          break;
+        }
+        mbar_arrive_expect_tx(&full[s], tile_bytes);
+        double* dst = tiles + (size_t)s * stage_doubles;
+        for (int q = 0; q < nbox; ++q) tma_load_2d(dst + (size_t)q * tr * boxw, &map, q * boxw, t * tr, &full[s]);
+      }
+      const int issued = k;
+      for (int kk = max(0, issued - S); kk < issued; ++kk)
+        mbar_wait_bounded(&full[kk % S], (kk / S) & 1, gtimer() + LS_WAIT_NS);
+    }
+    return;
+  }
+
+  if (warp < kRW) {
+    // ------------------------------------------------------------ row group
+    const int LPR = 32 / tr, CS = kRW * LPR;
+    const int rl = lane / LPR, q = lane - rl * LPR;
+    const int rho = LPR * ((warp + rl) % kRW) + q;
+    double rn2 = 0.0, dn2 = 0.0;
+    int k = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+      const int s = k % S;
+      bool ok = mbar_wait_bounded(&full[s], (k / S) & 1, gtimer() + LS_WAIT_NS);
+      if (ok && k >= 2) ok = mbar_wait_bounded(&rfree[k & 1], ((k >> 1) - 1) & 1, gtimer() + LS_WAIT_NS);
+      if (bar_any(!ok, 3, kRW * 32)) {                // the row group leaves together
+        if (!ok) atomicOr(a.status, LS_DEV_TIMEOUT);
+        break;
+      }
+      const double* tl = tiles + (size_t)s * stage_doubles;
+      const int64_t row0 = (int64_t)t * tr;
+      const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
+      double bj = 0.0, rpj = 0.0;
+      if (tid < rows) {                               // issue the row's loads before the dots
+        bj = a.b[row0 + tid];
+        if (a.r_prev) rpj = a.r_prev[row0 + tid];
+      }
+      // two accumulators: a dependent chain of FP64 FMAs issues one per FMA
+      // latency, so two interleaved chains keep the row group's pipe fed
+      double d0 = 0.0, d1 = 0.0;
+      if (rl < rows) {
+        int c = rho;
+        for (; c + CS < n; c += 2 * CS) {
+          d0 += tl[tile_off(rl, c, boxw, nbox, tr)] * xs[c];
+          d1 += tl[tile_off(rl, c + CS, boxw, nbox, tr)] * xs[c + CS];
+        }
+        if (c < n) d0 += tl[tile_off(rl, c, boxw, nbox, tr)] * xs[c];
+      }
+      double dot = d0 + d1;
+      for (int o = LPR >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      double* pk = p1 + (size_t)(k & 1) * kRW * tr;
+      if (q == 0) pk[warp * tr + rl] = dot;
+      asm volatile("bar.sync 2, %0;" ::"n"(kRW * 32));
+      if (tid < tr) {
+        double rj = 0.0;
+        if (tid < rows) {
+          double d = 0.0;
+#pragma unroll
+          for (int w = 0; w < kRW; ++w) d += pk[w * tr + tid];
+          rj = bj - d;
+          rn2 += rj * rj;
+          if (a.r_prev) { const double dl = rj - rpj; dn2 += dl * dl; }
+          if (a.r_out) a.r_out[row0 + tid] = rj;
+        }
+        rtile[(k & 1) * tr + tid] = rj;
+      }
+      if (warp == 0) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rready[k & 1]);
+      }
+    }
+    if (warp == 0) {
+      rn2 = warp_sum(rn2);
+      dn2 = warp_sum(dn2);
+      if (lane == 0) { out[n] = rn2; out[n + 1] = dn2; }
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- column group
+  const int tc = tid - kRW * 32;
+  constexpr int kCT2 = (kConsumerWarps - kRW) * 32;
+  double acc[NPT2];
+#pragma unroll
+  for (int u = 0; u < NPT2; ++u) acc[u] = 0.0;
+  int k = 0;
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+    const int s = k % S;
+    if (!mbar_wait_bounded(&full[s], (k / S) & 1, gtimer() + LS_WAIT_NS) ||
+        !mbar_wait_bounded(&rready[k & 1], (k >> 1) & 1, gtimer() + LS_WAIT_NS)) {
+      atomicOr(a.status, LS_DEV_TIMEOUT);
+      break;
+    }
+    const double* tl = tiles + (size_t)s * stage_doubles;
+    const double* rt = rtile + (k & 1) * tr;
+    const int64_t row0 = (int64_t)t * tr;
+    const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
+    for (int r = 0; r < rows; ++r) {
+      const double rj = rt[r];
+#pragma unroll
+      for (int u = 0; u < NPT2; ++u) {
+        const int c = tc + kCT2 * u;
+        if (c < n) acc[u] += tl[tile_off(r, c, boxw, nbox, tr)] * rj;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&rfree[k & 1]);
+      mbar_arrive(&empty[s]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NPT2; ++u) {
+    const int c = tc + kCT2 * u;
+    if (c < n) out[c] = acc[u];
+  }
 }
 
 // Sum the per-CTA partials in CTA order: c[k], norms[0..1].
@@ -356,7 +534,7 @@ PassGeom pass_geometry(const ls_ctx* ctx, int64_t n, int64_t m) {
   const int64_t ntiles = (m + g.tr - 1) / g.tr;
   g.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ntiles));
   g.smem = g.stages * stage + (size_t)((n + 1) & ~1LL) * 8 + 2 * g.tr * 8 + (2 * kConsumerWarps + 8) * 8 +
-           (size_t)kConsumerWarps * g.tr * 8 + 2 * g.stages * 8 + 128;
+           (size_t)kConsumerWarps * g.tr * 8 + 2 * g.stages * 8 + 4 * 8 + 128;
   // phase-2 group sums for n < 256 reuse the tile memory
   return g;
 }
@@ -394,6 +572,15 @@ static cudaError_t launch_pass_t(ls_ctx* ctx, const CUtensorMap& map, const Pass
   return cudaGetLastError();
 }
 
+template <int NPT2>
+static cudaError_t launch_pass_ws(ls_ctx* ctx, const CUtensorMap& map, const PassGeom& g, const PassArgs& a) {
+  cudaError_t e = cudaFuncSetAttribute(k_fused_pass_ws<NPT2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+  if (e != cudaSuccess) return e;
+  k_fused_pass_ws<NPT2><<<g.grid, kThreads, g.smem, ctx->stream>>>(map, a);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fused_pass(ls_ctx* ctx, const CUtensorMap& map, const PassGeom& g, int64_t m, int64_t n,
                               const double* b, const double* x, const double* r_prev, double* r_out, double* part,
                               const IterState* st) {
@@ -401,6 +588,12 @@ cudaError_t launch_fused_pass(ls_ctx* ctx, const CUtensorMap& map, const PassGeo
   a.m = m; a.n = (int)n; a.boxw = g.boxw; a.nbox = g.nbox; a.tr = g.tr; a.stages = g.stages;
   a.ntiles = (int)((m + g.tr - 1) / g.tr);
   a.b = b; a.x = x; a.r_prev = r_prev; a.r_out = r_out; a.part = part; a.st = st; a.status = ctx->d_status;
+  if (g.nbox > 1) {                      // n > 256: the warp-specialized form
+    const int npt2 = (int)((n + 127) / 128);
+    if (npt2 <= 8) return launch_pass_ws<8>(ctx, map, g, a);
+    if (npt2 <= 16) return launch_pass_ws<16>(ctx, map, g, a);
+    return cudaErrorInvalidValue;
+  }
   const int npt = (int)((n + 255) / 256);
   if (npt <= 1) return launch_pass_t<1>(ctx, map, g, a);
   if (npt <= 2) return launch_pass_t<2>(ctx, map, g, a);
