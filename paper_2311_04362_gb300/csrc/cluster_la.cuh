@@ -315,4 +315,187 @@ __device__ inline int power_steps(int n) {
   return k < 1 ? 1 : k;
 }
 
+
+// ------------------------------------------------- broadcast substitutions
+// The per-iteration pair of solves R^T y = c, R d = y (Algorithm 2's
+// preconditioned step) without a cluster-wide barrier inside a solve.
+//
+// Blocks of 32 rows are owned as above (block b by CTA b mod P) and, inside
+// the CTA, by warp pair q = (b / P) mod 4: warp 2q holds the row's sum over
+// columns 0..15 of every off-diagonal block, warp 2q+1 over columns 16..31
+// (a lane per row).  When block k's 32 solved entries land in a CTA's shared
+// memory (one mbarrier per block, completed by the bytes themselves), every
+// pair folds them into the rows it still has to solve.  The pair owning the
+// next block does so as soon as they land, adds its two halves, solves its
+// diagonal block in one warp and pushes the 32 results into every CTA with
+// st.async.  The operand slices of R for the next block are loaded while
+// the current one is waited for.
+//
+// Every row's inner product is summed in a fixed order (block by block, two
+// interleaved chains per half, then half 0 + half 1), so results are
+// reproducible; any fixed order keeps the substitution backward stable.
+constexpr int kTsMaxN = 2048;
+constexpr int kTsMaxBlocks = kTsMaxN / 32;
+constexpr int kTsMaxOwn = 8;         // diagonal blocks per CTA: n <= 256 P
+
+struct TsSmem {
+  double v[2][kTsMaxN];              // solved entries of each solve, every block pushed to every CTA
+  double dg[kTsMaxOwn][32 * 33];     // owned diagonal blocks: dg[o][i*33 + l] = R[32b + i, 32b + l], i <= l
+  double hs[2][kTsMaxOwn][32];       // half-1 sums handed to the half-0 warp
+  uint64_t bar[2][kTsMaxBlocks];     // bar[s][k]: block k of solve s has landed
+};
+
+__device__ inline int ts_owned(const CL& cl, int nb) {
+  return (nb - (int)cl.rank + (int)cl.ncta - 1) / (int)cl.ncta;
+}
+
+// Barriers for both solves and the owned diagonal blocks; call before the
+// cluster barrier that precedes the first solve.
+__device__ inline void ts_setup(const CL& cl, TsSmem& sm, const double* __restrict__ R, int64_t ldr, int n) {
+  const int nb = (n + 31) / 32;
+  if ((int)threadIdx.x < 2 * nb) {
+    const int sidx = threadIdx.x / nb, k = threadIdx.x % nb;
+    mbar_init(&sm.bar[sidx][k], 1);
+    mbar_arrive_expect_tx(&sm.bar[sidx][k], 8u * (uint32_t)min(32, n - 32 * k));
+  }
+  const int mine = ts_owned(cl, nb);
+  for (int idx = threadIdx.x; idx < mine * 1024; idx += blockDim.x) {
+    const int o = idx >> 10, l = (idx >> 5) & 31, i = idx & 31;
+    const int r0 = 32 * ((int)cl.rank + o * (int)cl.ncta);
+    sm.dg[o][i * 33 + l] = (i <= l && r0 + l < n) ? __ldg(R + (size_t)(r0 + i) + (size_t)(r0 + l) * ldr) : 0.0;
+  }
+  fence_mbar_init();
+}
+
+// Wait until every block of both solves has landed in this CTA (no st.async
+// may still be in flight towards it when it leaves).
+__device__ inline void ts_drain(TsSmem& sm, int n, uint64_t deadline, int& timed_out) {
+  const int nb = (n + 31) / 32;
+  if ((int)threadIdx.x < 2 * nb)
+    if (!mbar_wait_bounded(&sm.bar[threadIdx.x / nb][threadIdx.x % nb], 0, deadline)) timed_out = 1;
+}
+
+// One substitution.  kBack = false: R^T y = rhs with M = R^T column-major
+// (M[i + j*ldm] = R[j, i]); kBack = true: R x = rhs with M = R.  rhs[s] is
+// read by the half-0 lane of slot s (row 32 b_s + lane); out[s] receives the
+// solution there.  sidx selects the buffers (0 first solve, 1 second).
+template <int PP, bool kBack>
+__device__ inline void ts_solve(const CL& cl, TsSmem& sm, int sidx, const double* __restrict__ M, int64_t ldm,
+                                const double* __restrict__ inv_diag, int n, const double (&rhs)[PP],
+                                double (&out)[PP], uint64_t deadline, int& timed_out) {
+  const int nb = (n + 31) / 32, P = (int)cl.ncta;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, q = w >> 1, h = w & 1;
+  const int mine = ts_owned(cl, nb);
+  int bk[PP], row[PP];
+  bool has[PP], rowok[PP];
+  int klo = nb, khi = -1;
+#pragma unroll
+  for (int s = 0; s < PP; ++s) {
+    const int o = q + 4 * s;
+    has[s] = o < mine;
+    bk[s] = has[s] ? (int)cl.rank + o * P : -1;
+    row[s] = 32 * bk[s] + l;
+    rowok[s] = has[s] && row[s] < n;
+    out[s] = 0.0;
+    if (has[s]) { klo = min(klo, bk[s]); khi = max(khi, bk[s]); }
+  }
+  if (khi < 0) return;                          // this pair owns no block
+  // forward: blocks 0 .. khi; backward: nb-1 .. klo
+  const int kfirst = kBack ? nb - 1 : 0, kend = kBack ? klo - 1 : khi + 1, step = kBack ? -1 : 1;
+  double acc[PP], cur[PP][16], nxt[PP][16];
+  auto needs = [&](int s, int k) { return has[s] && (kBack ? k > bk[s] : k < bk[s]); };
+  auto load = [&](double (&dst)[PP][16], int k) {
+#pragma unroll
+    for (int s = 0; s < PP; ++s) {
+      const bool nd = needs(s, k) && rowok[s];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = 32 * k + 16 * h + j;
+        dst[s][j] = (nd && c < n) ? __ldg(M + (size_t)row[s] + (size_t)c * ldm) : 0.0;
+      }
+    }
+  };
+#pragma unroll
+  for (int s = 0; s < PP; ++s) acc[s] = 0.0;
+  load(cur, kfirst);
+  for (int k = kfirst; k != kend; k += step) {
+    if (k + step != kend) load(nxt, k + step);
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < PP; ++s) any = any || needs(s, k);
+    if (any) {
+      if (!mbar_wait_bounded(&sm.bar[sidx][k], 0, deadline)) timed_out = 1;
+      double vk[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = 32 * k + 16 * h + j;
+        vk[j] = c < n ? sm.v[sidx][c] : 0.0;
+      }
+#pragma unroll
+      for (int s = 0; s < PP; ++s)
+        if (needs(s, k)) {
+          double p0 = 0.0, p1 = 0.0;
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            p0 += cur[s][j] * vk[j];
+            p1 += cur[s][j + 1] * vk[j + 1];
+          }
+          acc[s] += p0 + p1;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < PP; ++s)
+      if (has[s] && k == bk[s]) {
+        const int o = q + 4 * s;
+        if (h == 1) sm.hs[sidx][o][l] = acc[s];
+        asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");
+        if (h == 0) {
+          double rv[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) rv[i] = kBack ? sm.dg[o][l * 33 + i] : sm.dg[o][i * 33 + l];
+          const double inv = rowok[s] ? __ldg(inv_diag + row[s]) : 0.0;
+          double wl = rowok[s] ? rhs[s] - (acc[s] + sm.hs[sidx][o][l]) : 0.0;
+          double yl = 0.0;
+          if (!kBack) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const double yi = __shfl_sync(0xffffffffu, wl * inv, i);
+              if (l == i) yl = yi;
+              if (l > i) wl = wl - rv[i] * yi;
+            }
+          } else {
+#pragma unroll
+            for (int i = 31; i >= 0; --i) {
+              const double yi = __shfl_sync(0xffffffffu, wl * inv, i);
+              if (l == i) yl = yi;
+              if (l < i) wl = wl - rv[i] * yi;
+            }
+          }
+          out[s] = yl;
+          if (rowok[s]) {
+            const uint32_t va = smem_u32(&sm.v[sidx][row[s]]), ba = smem_u32(&sm.bar[sidx][k]);
+            for (int d = 0; d < P; ++d) {
+              uint32_t ra, rb;
+              asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(va), "r"(d));
+              asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rb) : "r"(ba), "r"(d));
+              st_async_f64(ra, yl, rb);
+            }
+          }
+        }
+      }
+    if (k + step != kend) {
+#pragma unroll
+      for (int s = 0; s < PP; ++s)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) cur[s][j] = nxt[s][j];
+    }
+  }
+}
+
+// Pairs-per-slot needed for n on a cluster of P CTAs (0: too large).
+__host__ __device__ inline int ts_slots(int n, int P) {
+  const int nb = (n + 31) / 32, mine = (nb + P - 1) / P;
+  return mine <= 4 ? 1 : mine <= 8 ? 2 : 0;
+}
+
 }  // namespace lsk

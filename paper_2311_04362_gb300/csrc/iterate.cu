@@ -430,10 +430,14 @@ __device__ inline double part_sum(const double* part, int nparts, int n, int k) 
   return s;
 }
 
+template <int PP>
 __global__ void __launch_bounds__(256) k_iter_step(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char ts_raw[];
+  TsSmem& sm = *reinterpret_cast<TsSmem*>(ts_raw);
   const CL cl = cl_this();
   const int n = a.n;
   IterState S = *a.st;       // every CTA reads the state before anyone writes it
+  if (!S.done) ts_setup(cl, sm, a.R, a.ldr, n);
   cl_sync();
   if (S.done) return;
 
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(256) k_iter_step(StepArgs a) {
     if (extra_left == 0) done = 1;
     else extra_left -= 1;
   }
-  if (done) {
+  if (done) {                // uniform over the cluster; nothing has been pushed yet
     if (cl.rank == 0 && threadIdx.x == 0) {
       a.st->done = 1; a.st->fired = 1; a.st->stop_reason = 0;
       a.st->rnorm = rnorm; a.st->dnorm = dnorm;
@@ -463,23 +467,38 @@ __global__ void __launch_bounds__(256) k_iter_step(StepArgs a) {
     return;
   }
 
-  // c = sum of partials for the owned rows -> forward solve y = R^{-T} c
-  for_owned_rows(cl, n, [&](int i) { __stcg(a.work + i, part_sum(a.part, a.nparts, n, i)); });
-  __syncthreads();
-  cl_solve_RT(cl, a.Rt, n, a.inv_diag, a.work, a.y);
-  cl_load_owned(cl, n, a.y, a.work);
-  cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, a.dvec);
+  // c = sum of partials on the owned rows; y = R^{-T} c; d = R^{-1} y
+  const uint64_t deadline = gtimer() + 2000000000ull;
+  int tmo = 0;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, q = w >> 1, h = w & 1;
+  const int nb = (n + 31) / 32, mine = ts_owned(cl, nb);
+  double c[PP], y[PP], dv[PP];
+#pragma unroll
+  for (int s = 0; s < PP; ++s) {
+    const int o = q + 4 * s, i = 32 * ((int)cl.rank + o * (int)cl.ncta) + l;
+    c[s] = (h == 0 && o < mine && i < n) ? part_sum(a.part, a.nparts, n, i) : 0.0;
+  }
+  ts_solve<PP, false>(cl, sm, 0, a.Rt, n, a.inv_diag, n, c, y, deadline, tmo);
+  ts_solve<PP, true>(cl, sm, 1, a.R, a.ldr, a.inv_diag, n, y, dv, deadline, tmo);
 
   // x+ = x + alpha d + beta (x - x_prev) on owned rows; ||x+||^2
   double xs = 0.0, bad = 0.0;
-  for_owned_rows(cl, n, [&](int i) {
-    const double xi = __ldcg(a.x + i), xp = __ldcg(a.x_prev + i), di = __ldcg(a.dvec + i);
-    const double xn = xi + S.alpha * di + S.beta * (xi - xp);
-    __stcg(a.x_prev + i, xi);
-    __stcg(a.x + i, xn);
-    xs += xn * xn;
-    if (!isfinite(xn)) bad = 1.0;
-  });
+  if (h == 0) {
+#pragma unroll
+    for (int s = 0; s < PP; ++s) {
+      const int o = q + 4 * s, i = 32 * ((int)cl.rank + o * (int)cl.ncta) + l;
+      if (o < mine && i < n) {
+        const double xi = __ldcg(a.x + i), xp = __ldcg(a.x_prev + i);
+        const double xn = xi + S.alpha * dv[s] + S.beta * (xi - xp);
+        __stcg(a.x_prev + i, xi);
+        __stcg(a.x + i, xn);
+        xs += xn * xn;
+        if (!isfinite(xn)) bad = 1.0;
+      }
+    }
+  }
+  ts_drain(sm, n, deadline, tmo);
+  if (tmo) atomicOr(a.status, LS_DEV_TIMEOUT);
   const double xn2 = cl_sum(cl, cta_sum(xs), a.slots);
   const double anybad = cl_max(cl, cta_max(bad), a.slots);
   if (cl.rank == 0 && threadIdx.x == 0) {
@@ -498,19 +517,40 @@ __global__ void __launch_bounds__(256) k_iter_step(StepArgs a) {
 }
 
 // y = R^{-T} c, d = R^{-1} y, x += d (standalone correction).
+template <int PP>
 __global__ void __launch_bounds__(256) k_correct(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char ts_raw[];
+  TsSmem& sm = *reinterpret_cast<TsSmem*>(ts_raw);
   const CL cl = cl_this();
   const int n = a.n;
-  cl_load_owned(cl, n, a.c_in, a.work);
-  cl_solve_RT(cl, a.Rt, n, a.inv_diag, a.work, a.y);
-  cl_load_owned(cl, n, a.y, a.work);
-  cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, a.dvec);
-  for_owned_rows(cl, n, [&](int i) {
-    const double di = __ldcg(a.dvec + i);
-    __stcg(a.x + i, __ldcg(a.x + i) + di);
-    if (a.y_out) a.y_out[i] = __ldcg(a.y + i);
-    if (a.d_out) a.d_out[i] = di;
-  });
+  ts_setup(cl, sm, a.R, a.ldr, n);
+  cl_sync();
+  const uint64_t deadline = gtimer() + 2000000000ull;
+  int tmo = 0;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, q = w >> 1, h = w & 1;
+  const int nb = (n + 31) / 32, mine = ts_owned(cl, nb);
+  double c[PP], y[PP], dv[PP];
+#pragma unroll
+  for (int s = 0; s < PP; ++s) {
+    const int o = q + 4 * s, i = 32 * ((int)cl.rank + o * (int)cl.ncta) + l;
+    c[s] = (h == 0 && o < mine && i < n) ? __ldcg(a.c_in + i) : 0.0;
+  }
+  ts_solve<PP, false>(cl, sm, 0, a.Rt, n, a.inv_diag, n, c, y, deadline, tmo);
+  ts_solve<PP, true>(cl, sm, 1, a.R, a.ldr, a.inv_diag, n, y, dv, deadline, tmo);
+  if (h == 0) {
+#pragma unroll
+    for (int s = 0; s < PP; ++s) {
+      const int o = q + 4 * s, i = 32 * ((int)cl.rank + o * (int)cl.ncta) + l;
+      if (o < mine && i < n) {
+        __stcg(a.x + i, __ldcg(a.x + i) + dv[s]);
+        if (a.y_out) a.y_out[i] = y[s];
+        if (a.d_out) a.d_out[i] = dv[s];
+      }
+    }
+  }
+  ts_drain(sm, n, deadline, tmo);
+  if (tmo) atomicOr(a.status, LS_DEV_TIMEOUT);
+  cl_sync();
 }
 
 // ------------------------------------------------------------ host side
@@ -611,16 +651,68 @@ cudaError_t launch_reduce_partials(ls_ctx* ctx, const double* part, int nparts, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_iter_step(ls_ctx* ctx, const StepArgs& a) {
+// Cluster size for the broadcast substitutions: 16 CTAs where the device
+// can hold such a cluster with the solve's shared memory, else 8.
+int ts_cluster_size() {
+  static int size = -1;
+  if (size > 0) return size;
+  const void* fns[] = {(const void*)k_iter_step<1>, (const void*)k_iter_step<2>, (const void*)k_correct<1>,
+                       (const void*)k_correct<2>};
+  bool ok16 = true;
+  for (const void* f : fns) {
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TsSmem));
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) ok16 = false;
+  }
+  cudaGetLastError();
+  if (ok16) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = sizeof(TsSmem);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    for (const void* f : fns)
+      if (cudaOccupancyMaxActiveClusters(&nclusters, f, &cfg) != cudaSuccess || nclusters < 1) ok16 = false;
+    cudaGetLastError();
+  }
+  size = ok16 ? 16 : 8;
+  return size;
+}
+
+static cudaError_t launch_ts(ls_ctx* ctx, const void* f1, const void* f2, const StepArgs& a) {
+  const int P = ts_cluster_size();
+  const int pp = ts_slots(a.n, P);
+  if (pp == 0 || a.n > kTsMaxN) return cudaErrorInvalidValue;
   StepArgs aa = a;
   void* args[] = {&aa};
-  return launch_cluster(ctx, (const void*)k_iter_step, args, ctx->cluster);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = sizeof(TsSmem);
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++ctx->launches;
+  return cudaLaunchKernelExC(&cfg, pp == 1 ? f1 : f2, args);
+}
+
+cudaError_t launch_iter_step(ls_ctx* ctx, const StepArgs& a) {
+  return launch_ts(ctx, (const void*)k_iter_step<1>, (const void*)k_iter_step<2>, a);
 }
 
 cudaError_t launch_correct(ls_ctx* ctx, const StepArgs& a) {
-  StepArgs aa = a;
-  void* args[] = {&aa};
-  return launch_cluster(ctx, (const void*)k_correct, args, ctx->cluster);
+  return launch_ts(ctx, (const void*)k_correct<1>, (const void*)k_correct<2>, a);
 }
 
 }  // namespace lsk

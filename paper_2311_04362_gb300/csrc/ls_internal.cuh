@@ -164,6 +164,14 @@ __device__ inline double ld_cluster_f64(uint32_t addr) {
   return v;
 }
 
+// Store v into the shared memory of a cluster peer (addresses from
+// map_shared); the 8 bytes count toward the peer's mbarrier transaction.
+__device__ inline void st_async_f64(uint32_t addr, double v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+               "l"(__double_as_longlong(v)), "r"(bar)
+               : "memory");
+}
+
 // ------------------------------------------------------------- grid barrier
 // Sense-free generation barrier for a cooperative launch (all CTAs are
 // co-resident).  Every wait is bounded; on timeout the status word gets
