@@ -334,13 +334,25 @@ __device__ inline int power_steps(int n) {
 // Every row's inner product is summed in a fixed order (block by block, two
 // interleaved chains per half, then half 0 + half 1), so results are
 // reproducible; any fixed order keeps the substitution backward stable.
+//
+// A diagonal block D is solved as the unit-triangular system with D's
+// off-diagonal entries divided by their pivots (D = U diag(D) for R^T, the
+// columns of R for R itself), then each entry is multiplied by 1 / D_ii.
+// Each of the 32 sequential steps is then one FP64 FMA and a shuffle instead
+// of a multiply, a shuffle and an FMA: an FP64 warp instruction occupies a
+// GB300 sub-partition for 64 cycles however many lanes it uses, so the
+// chain is bound by its FP64 instruction count.  The scaled entries carry
+// one extra rounding each, a componentwise relative perturbation of u, so
+// the substitution stays backward stable.
 constexpr int kTsMaxN = 2048;
 constexpr int kTsMaxBlocks = kTsMaxN / 32;
 constexpr int kTsMaxOwn = 8;         // diagonal blocks per CTA: n <= 256 P
 
 struct TsSmem {
   double v[2][kTsMaxN];              // solved entries of each solve, every block pushed to every CTA
-  double dg[kTsMaxOwn][32 * 33];     // owned diagonal blocks: dg[o][i*33 + l] = R[32b + i, 32b + l], i <= l
+  double dg[2][kTsMaxOwn][32 * 33];  // owned diagonal blocks, scaled by the pivots:
+                                     //   dg[0][o][i*33 + l] = R[32b+i, 32b+l] / R[32b+i, 32b+i], i < l
+                                     //   dg[1][o][l*33 + i] = R[32b+l, 32b+i] / R[32b+i, 32b+i], l < i
   double hs[2][kTsMaxOwn][32];       // half-1 sums handed to the half-0 warp
   uint64_t bar[2][kTsMaxBlocks];     // bar[s][k]: block k of solve s has landed
 };
@@ -351,7 +363,8 @@ __device__ inline int ts_owned(const CL& cl, int nb) {
 
 // Barriers for both solves and the owned diagonal blocks; call before the
 // cluster barrier that precedes the first solve.
-__device__ inline void ts_setup(const CL& cl, TsSmem& sm, const double* __restrict__ R, int64_t ldr, int n) {
+__device__ inline void ts_setup(const CL& cl, TsSmem& sm, const double* __restrict__ R, int64_t ldr,
+                                const double* __restrict__ inv_diag, int n) {
   const int nb = (n + 31) / 32;
   if ((int)threadIdx.x < 2 * nb) {
     const int sidx = threadIdx.x / nb, k = threadIdx.x % nb;
@@ -362,7 +375,11 @@ __device__ inline void ts_setup(const CL& cl, TsSmem& sm, const double* __restri
   for (int idx = threadIdx.x; idx < mine * 1024; idx += blockDim.x) {
     const int o = idx >> 10, l = (idx >> 5) & 31, i = idx & 31;
     const int r0 = 32 * ((int)cl.rank + o * (int)cl.ncta);
-    sm.dg[o][i * 33 + l] = (i <= l && r0 + l < n) ? __ldg(R + (size_t)(r0 + i) + (size_t)(r0 + l) * ldr) : 0.0;
+    // R[r0+i, r0+l] (i < l) scaled by its row's pivot (forward) and by its column's (backward)
+    const bool in = i < l && r0 + l < n;
+    const double v = in ? __ldg(R + (size_t)(r0 + i) + (size_t)(r0 + l) * ldr) : 0.0;
+    sm.dg[0][o][i * 33 + l] = in ? v * __ldg(inv_diag + r0 + i) : 0.0;
+    sm.dg[1][o][i * 33 + l] = in ? v * __ldg(inv_diag + r0 + l) : 0.0;
   }
   fence_mbar_init();
 }
@@ -402,7 +419,7 @@ __device__ inline void ts_solve(const CL& cl, TsSmem& sm, int sidx, const double
   if (khi < 0) return;                          // this pair owns no block
   // forward: blocks 0 .. khi; backward: nb-1 .. klo
   const int kfirst = kBack ? nb - 1 : 0, kend = kBack ? klo - 1 : khi + 1, step = kBack ? -1 : 1;
-  double acc[PP], cur[PP][16], nxt[PP][16];
+  double acc[PP], cur[PP][16], nxt[PP][16], inv[PP];
   auto needs = [&](int s, int k) { return has[s] && (kBack ? k > bk[s] : k < bk[s]); };
   auto load = [&](double (&dst)[PP][16], int k) {
 #pragma unroll
@@ -416,7 +433,10 @@ __device__ inline void ts_solve(const CL& cl, TsSmem& sm, int sidx, const double
     }
   };
 #pragma unroll
-  for (int s = 0; s < PP; ++s) acc[s] = 0.0;
+  for (int s = 0; s < PP; ++s) {
+    acc[s] = 0.0;
+    inv[s] = (h == 0 && rowok[s]) ? __ldg(inv_diag + row[s]) : 0.0;
+  }
   load(cur, kfirst);
   for (int k = kfirst; k != kend; k += step) {
     if (k + step != kend) load(nxt, k + step);
@@ -450,27 +470,25 @@ __device__ inline void ts_solve(const CL& cl, TsSmem& sm, int sidx, const double
         if (h == 1) sm.hs[sidx][o][l] = acc[s];
         asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");
         if (h == 0) {
+          // lane l: row l of the unit-triangular block (column l of the scaled R)
           double rv[32];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) rv[i] = kBack ? sm.dg[o][l * 33 + i] : sm.dg[o][i * 33 + l];
-          const double inv = rowok[s] ? __ldg(inv_diag + row[s]) : 0.0;
+          for (int i = 0; i < 32; ++i) rv[i] = kBack ? sm.dg[1][o][l * 33 + i] : sm.dg[0][o][i * 33 + l];
           double wl = rowok[s] ? rhs[s] - (acc[s] + sm.hs[sidx][o][l]) : 0.0;
-          double yl = 0.0;
           if (!kBack) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-              const double yi = __shfl_sync(0xffffffffu, wl * inv, i);
-              if (l == i) yl = yi;
-              if (l > i) wl = wl - rv[i] * yi;
+              const double wi = __shfl_sync(0xffffffffu, wl, i);
+              if (l > i) wl = wl - rv[i] * wi;
             }
           } else {
 #pragma unroll
             for (int i = 31; i >= 0; --i) {
-              const double yi = __shfl_sync(0xffffffffu, wl * inv, i);
-              if (l == i) yl = yi;
-              if (l < i) wl = wl - rv[i] * yi;
+              const double wi = __shfl_sync(0xffffffffu, wl, i);
+              if (l < i) wl = wl - rv[i] * wi;
             }
           }
+          const double yl = wl * inv[s];
           out[s] = yl;
           if (rowok[s]) {
             const uint32_t va = smem_u32(&sm.v[sidx][row[s]]), ba = smem_u32(&sm.bar[sidx][k]);

@@ -268,16 +268,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass_ws(const __grid_cons
   const size_t stage_doubles = (size_t)tr * nbox * boxw;
   double* tiles = reinterpret_cast<double*>(smem_raw);
   double* xs = tiles + S * stage_doubles;
-  double* rtile = xs + ((n + 1) & ~1);              // [2][tr]
-  double* red = rtile + 2 * tr;
+  double* rtile = xs + ((n + 1) & ~1);              // [S][tr]
+  double* red = rtile + 4 * tr;
   double* p1 = red + 2 * kConsumerWarps + 8;        // [2][kRW][tr] row-dot partials
   uint64_t* full = reinterpret_cast<uint64_t*>(p1 + kConsumerWarps * tr);
   uint64_t* empty = full + S;
-  uint64_t* rready = empty + S;                     // [2] r of a tile written
-  uint64_t* rfree = rready + 2;                     // [2] r of a tile consumed
+  uint64_t* rready = empty + S;                     // [S] r of a tile written
+  uint64_t* rfree = rready + S;                     // [S] r of a tile consumed
   if (tid == 0) {
     for (int s = 0; s < S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], kConsumerWarps - kRW); }
-    for (int i = 0; i < 2; ++i) { mbar_init(&rready[i], 1); mbar_init(&rfree[i], kConsumerWarps - kRW); }
+    for (int i = 0; i < S; ++i) { mbar_init(&rready[i], 1); mbar_init(&rfree[i], kConsumerWarps - kRW); }
     fence_mbar_init();
   }
   for (int i = tid; i < n; i += blockDim.x) xs[i] = a.x[i];
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass_ws(const __grid_cons
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
       const int s = k % S;
       bool ok = mbar_wait_bounded(&full[s], (k / S) & 1, gtimer() + LS_WAIT_NS);
-      if (ok && k >= 2) ok = mbar_wait_bounded(&rfree[k & 1], ((k >> 1) - 1) & 1, gtimer() + LS_WAIT_NS);
+      if (ok && k >= S) ok = mbar_wait_bounded(&rfree[s], ((k / S) - 1) & 1, gtimer() + LS_WAIT_NS);
       if (bar_any(!ok, 3, kRW * 32)) {                // the row group leaves together
         if (!ok) atomicOr(a.status, LS_DEV_TIMEOUT);
         break;
@@ -357,11 +357,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass_ws(const __grid_cons
           if (a.r_prev) { const double dl = rj - rpj; dn2 += dl * dl; }
           if (a.r_out) a.r_out[row0 + tid] = rj;
         }
-        rtile[(k & 1) * tr + tid] = rj;
+        rtile[s * tr + tid] = rj;
       }
       if (warp == 0) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(&rready[k & 1]);
+        if (lane == 0) mbar_arrive(&rready[s]);
       }
     }
     if (warp == 0) {
@@ -382,12 +382,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass_ws(const __grid_cons
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
     const int s = k % S;
     if (!mbar_wait_bounded(&full[s], (k / S) & 1, gtimer() + LS_WAIT_NS) ||
-        !mbar_wait_bounded(&rready[k & 1], (k >> 1) & 1, gtimer() + LS_WAIT_NS)) {
+        !mbar_wait_bounded(&rready[s], (k / S) & 1, gtimer() + LS_WAIT_NS)) {
       atomicOr(a.status, LS_DEV_TIMEOUT);
       break;
     }
     const double* tl = tiles + (size_t)s * stage_doubles;
-    const double* rt = rtile + (k & 1) * tr;
+    const double* rt = rtile + s * tr;
     const int64_t row0 = (int64_t)t * tr;
     const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
     for (int r = 0; r < rows; ++r) {
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass_ws(const __grid_cons
     }
     __syncwarp();
     if (lane == 0) {
-      mbar_arrive(&rfree[k & 1]);
+      mbar_arrive(&rfree[s]);
       mbar_arrive(&empty[s]);
     }
   }
@@ -437,13 +437,21 @@ __global__ void __launch_bounds__(256) k_iter_step(StepArgs a) {
   const CL cl = cl_this();
   const int n = a.n;
   IterState S = *a.st;       // every CTA reads the state before anyone writes it
-  if (!S.done) ts_setup(cl, sm, a.R, a.ldr, n);
+  if (!S.done) ts_setup(cl, sm, a.R, a.ldr, a.inv_diag, n);
   cl_sync();
   if (S.done) return;
 
   // ||r_i||, ||r_i - r_{i-1}|| (every CTA computes them identically)
+  // (warp w < 2 sums column n + w: lane j takes the partials j, j + 32, ...,
+  // then a fixed butterfly)
   __shared__ double s_norm[2];
-  if (threadIdx.x < 2) s_norm[threadIdx.x] = part_sum(a.part, a.nparts, n, n + threadIdx.x);
+  if (threadIdx.x < 64) {
+    const int col = n + (threadIdx.x >> 5);
+    double t = 0.0;
+    for (int p = threadIdx.x & 31; p < a.nparts; p += 32) t += __ldcg(a.part + (size_t)p * (n + 2) + col);
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) s_norm[threadIdx.x >> 5] = t;
+  }
   __syncthreads();
   const double rnorm = sqrt(s_norm[0]);
   const double dnorm = S.have_prev ? sqrt(s_norm[1]) : 0.0;
@@ -523,7 +531,7 @@ __global__ void __launch_bounds__(256) k_correct(StepArgs a) {
   TsSmem& sm = *reinterpret_cast<TsSmem*>(ts_raw);
   const CL cl = cl_this();
   const int n = a.n;
-  ts_setup(cl, sm, a.R, a.ldr, n);
+  ts_setup(cl, sm, a.R, a.ldr, a.inv_diag, n);
   cl_sync();
   const uint64_t deadline = gtimer() + 2000000000ull;
   int tmo = 0;
@@ -567,14 +575,14 @@ PassGeom pass_geometry(const ls_ctx* ctx, int64_t n, int64_t m) {
   } else {
     g.boxw = 256;
     g.nbox = (int)((n + 255) / 256);
-    g.tr = (g.nbox <= 4) ? 8 : 4;
+    g.tr = (g.nbox <= 2) ? 16 : (g.nbox <= 4) ? 8 : 4;
   }
   const size_t stage = (size_t)g.tr * g.nbox * g.boxw * sizeof(double);
   g.stages = (int)std::max<size_t>(2, std::min<size_t>(4, (200 * 1024) / stage));
   const int64_t ntiles = (m + g.tr - 1) / g.tr;
   g.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ntiles));
-  g.smem = g.stages * stage + (size_t)((n + 1) & ~1LL) * 8 + 2 * g.tr * 8 + (2 * kConsumerWarps + 8) * 8 +
-           (size_t)kConsumerWarps * g.tr * 8 + 2 * g.stages * 8 + 4 * 8 + 128;
+  g.smem = g.stages * stage + (size_t)((n + 1) & ~1LL) * 8 + 4 * g.tr * 8 + (2 * kConsumerWarps + 8) * 8 +
+           (size_t)kConsumerWarps * g.tr * 8 + 4 * g.stages * 8 + 128;
   // phase-2 group sums for n < 256 reuse the tile memory
   return g;
 }
