@@ -135,13 +135,17 @@ __global__ void __launch_bounds__(256) k_householder(double* __restrict__ B, int
 //   * the panel slice of this CTA's rows is factored in shared memory, one
 //     column at a time (two grid barriers per column: norm partials, then dot
 //     partials), exactly the unblocked steps restricted to the panel;
-//   * T (kNB x kNB, upper triangular) from G = V^T V: T[b][b] = tau_b,
-//     T[0:b, b] = -tau_b T[0:b, 0:b] G[0:b, b];
-//   * the trailing columns (including S b) get C <- C - V (T^T (V^T C)):
-//     W = V^T C as per-CTA partials summed in CTA order, W' = T^T W, then
-//     every CTA updates its own rows.  Both products run thread-per-column
-//     with kNB FP64 accumulators in registers and V broadcast from shared
-//     memory.
+//   * the trailing columns (including S b) get C <- C - V (T^T (V^T C))
+//     with T the Schreiber-Van Loan factor (T[b][b] = tau_b,
+//     T[0:b, b] = -tau_b T[0:b, 0:b] G[0:b, b], G = V^T V).  T is not
+//     formed: T^{-1} = diag(1 / tau) + striu(G), so W' = T^T W is a forward
+//     substitution with G.  W = V^T C is summed over CTAs in CTA order, G's
+//     strict upper triangle is summed by CTA e mod P for entry e (one more
+//     grid barrier), and every CTA updates its own rows.  The products run
+//     on (32 columns, quarter) tasks with V broadcast from shared memory:
+//     an FP64 warp instruction costs its sub-partition the same time however
+//     many lanes are active, so work is dealt in whole warps, evenly over the
+//     four sub-partitions.
 static constexpr int kNB = 32;
 
 struct HhArgs {
@@ -282,78 +286,107 @@ __global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
     __syncthreads();
 
     // ---------------------------------------------------- partial G and W = V^T C
+    // G: the 496 entries r < c of V^T V over own rows, packed as
+    // e = c (c - 1) / 2 + r; 16 lane sets of 32 entries, two per warp, so that
+    // every lane has work.  W: tasks (group of 32 columns, quarter h of the
+    // kNB reflectors); warp w takes quarter w mod 4 of every other group, so
+    // each sub-partition gets the same number of FP64 instructions.
     const int i0 = (int)max((int64_t)0, (int64_t)k0 - r0);
-    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
-      const int r = e / kNB, c = e - r * kNB;
-      double s = 0.0;
-      if (r < c && c < nbp)
-        for (int i = i0; i < nrow; ++i) s += Ps[r * ldp + i] * Ps[c * ldp + i];
-      __stcg(pG + (size_t)p * kNB * kNB + e, s);
+    for (int ls = 2 * warp; ls < 2 * warp + 2; ++ls) {
+      const int e = 32 * ls + lane;
+      if (e < kNB * (kNB - 1) / 2) {
+        int c = 1;
+        while ((c + 1) * c / 2 <= e) ++c;
+        const int r = e - c * (c - 1) / 2;
+        double g = 0.0;
+        if (c < nbp)
+          for (int i = i0; i < nrow; ++i) g += Ps[r * ldp + i] * Ps[c * ldp + i];
+        __stcg(pG + (size_t)p * kNB * kNB + e, g);
+      }
     }
     const int jt0 = k0 + nbp;
-    for (int j = jt0 + threadIdx.x; j < ncols; j += blockDim.x) {
-      double acc[kNB];
+    const int ngroups = (ncols - jt0 + 31) / 32;
+    {
+      const int h = warp & 3;
+      for (int g = warp >> 2; g < ngroups; g += 2) {
+        const int j = jt0 + 32 * g + lane;
+        if (j < ncols) {
+          double acc[kNB / 4];
 #pragma unroll
-      for (int q = 0; q < kNB; ++q) acc[q] = 0.0;
-      const double* cp = B + (int64_t)j * ldb + r0;
-      for (int i = i0; i < nrow; ++i) {
-        const double c = cp[i];
+          for (int q = 0; q < kNB / 4; ++q) acc[q] = 0.0;
+          const double* cp = B + (int64_t)j * ldb + r0;
+          const double* vp = Ps + (size_t)(h * (kNB / 4)) * ldp;
+#pragma unroll 2
+          for (int i = i0; i < nrow; ++i) {
+            const double c = cp[i];
 #pragma unroll
-        for (int q = 0; q < kNB; ++q) acc[q] += Ps[q * ldp + i] * c;
+            for (int q = 0; q < kNB / 4; ++q) acc[q] += vp[q * ldp + i] * c;
+          }
+          double* out = pW + ((size_t)p * kNB + h * (kNB / 4)) * ncols + j;
+#pragma unroll
+          for (int q = 0; q < kNB / 4; ++q) __stcg(out + (size_t)q * ncols, acc[q]);
+        }
       }
-      double* out = pW + (size_t)p * kNB * ncols + j;
-#pragma unroll
-      for (int q = 0; q < kNB; ++q) __stcg(out + (size_t)q * ncols, acc[q]);
     }
     if (!grid_sync(a.gb, P)) return;
 
-    // ---------------------------------------------------- T (every CTA), W' = T^T W
+    // ---------------------------------------------------- G summed over CTAs (CTA p: entries p, p + P, ...)
+    double* Gred = a.Wp + (size_t)kNB * ncols + 8;
+    for (int e = p + warp * P; e < kNB * (kNB - 1) / 2; e += nwarp * P) {
+      double g = 0.0;
+      for (int q = lane; q < P; q += 32) g += __ldcg(pG + (size_t)q * kNB * kNB + e);
+      g = warp_sum(g);
+      if (lane == 0) __stcg(Gred + e, g);
+    }
+    if (!grid_sync(a.gb, P)) return;
+
+    // ---------------------------------------------------- W' = T^T W
+    // T^{-1} = diag(1 / tau) + striu(V^T V) (Schreiber-Van Loan T, in the
+    // Puglisi form), so W' solves (diag(1 / tau) + striu(G))^T W' = W by
+    // forward substitution over the reflectors: W'_q = tau_q (W_q -
+    // sum_{r<q} G_rq W'_r).  With M_rq = G_rq tau_r each step is one FMA:
+    // lane q keeps W_q - sum_r M_rq (W_r - ...), scaled by tau_q at the end.
     for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
-      double s = 0.0;
-      for (int q = 0; q < P; ++q) s += __ldcg(pG + (size_t)q * kNB * kNB + e);
-      Gs[e] = s;
+      const int r = e / kNB, q = e - r * kNB;
+      double mv = 0.0;
+      if (r < q && q < nbp) mv = __ldcg(Gred + q * (q - 1) / 2 + r) * s_tau[r];
+      Gs[e] = mv;
     }
     __syncthreads();
-    if (warp == 0) {
-      const int r = lane;
-      for (int c = 0; c < kNB; ++c) {
-        double t = 0.0;
-        if (c < nbp) {
-          if (r == c) t = s_tau[c];
-          else if (r < c) {
-            double s = 0.0;
-            for (int q = r; q < c; ++q) s += Ts[r * kNB + q] * Gs[q * kNB + c];
-            t = -s_tau[c] * s;
-          }
+    {
+      const double tq = (lane < nbp) ? s_tau[lane] : 0.0;
+      for (int j = jt0 + p * nwarp + warp; j < ncols; j += P * nwarp) {
+        double w = 0.0;
+        for (int q = 0; q < P; ++q) w += __ldcg(pW + ((size_t)q * kNB + lane) * ncols + j);
+        for (int r = 0; r + 1 < nbp; ++r) {
+          const double t = __shfl_sync(0xffffffffu, w, r);
+          if (lane > r) w = w - Gs[r * kNB + lane] * t;
         }
-        Ts[r * kNB + c] = t;
-        __syncwarp();
+        __stcg(a.Wp + (size_t)lane * ncols + j, w * tq);
       }
-    }
-    __syncthreads();
-    for (int j = jt0 + p * nwarp + warp; j < ncols; j += P * nwarp) {
-      double w = 0.0;
-      for (int q = 0; q < P; ++q) w += __ldcg(pW + ((size_t)q * kNB + lane) * ncols + j);
-      double wp = 0.0;
-      for (int b = 0; b < kNB; ++b) {
-        const double wb = __shfl_sync(0xffffffffu, w, b);
-        if (b <= lane) wp += Ts[b * kNB + lane] * wb;
-      }
-      __stcg(a.Wp + (size_t)lane * ncols + j, wp);
     }
     if (!grid_sync(a.gb, P)) return;
 
     // ---------------------------------------------------- C -= V W' on own rows
-    for (int j = jt0 + threadIdx.x; j < ncols; j += blockDim.x) {
-      double wv[kNB];
+    // tasks (group of 32 columns, quarter h of the rows i0..nrow)
+    {
+      const int h = warp & 3;
+      const int len = nrow - i0;
+      const int ia = i0 + (int)(((int64_t)len * h) / 4), ib = i0 + (int)(((int64_t)len * (h + 1)) / 4);
+      for (int g = warp >> 2; g < ngroups; g += 2) {
+        const int j = jt0 + 32 * g + lane;
+        if (j < ncols && ia < ib) {
+          double wv[kNB];
 #pragma unroll
-      for (int q = 0; q < kNB; ++q) wv[q] = __ldcg(a.Wp + (size_t)q * ncols + j);
-      double* cp = B + (int64_t)j * ldb + r0;
-      for (int i = i0; i < nrow; ++i) {
-        double c = cp[i];
+          for (int q = 0; q < kNB; ++q) wv[q] = __ldcg(a.Wp + (size_t)q * ncols + j);
+          double* cp = B + (int64_t)j * ldb + r0;
+          for (int i = ia; i < ib; ++i) {
+            double c = cp[i];
 #pragma unroll
-        for (int q = 0; q < kNB; ++q) c -= Ps[q * ldp + i] * wv[q];
-        cp[i] = c;
+            for (int q = 0; q < kNB; ++q) c -= Ps[q * ldp + i] * wv[q];
+            cp[i] = c;
+          }
+        }
       }
     }
     __syncthreads();
@@ -544,7 +577,7 @@ size_t householder_part_doubles(const ls_ctx* ctx, int64_t d, int64_t n) {
   return std::max(unblocked, blocked);
 }
 
-size_t householder_w_doubles(int64_t n) { return (size_t)kNB * (size_t)(n + 1) + 8; }
+size_t householder_w_doubles(int64_t n) { return (size_t)kNB * (size_t)(n + 1) + 8 + kNB * kNB; }
 
 cudaError_t launch_cluster(ls_ctx* ctx, const void* fn, void** args, int cluster) {
   cudaLaunchConfig_t cfg = {};
