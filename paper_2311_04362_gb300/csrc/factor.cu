@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   double* B = a.B;
   const int64_t ldb = a.ldb;
+  MonoBar mb{a.gb.count, a.gb.status, 0u};
 
   // norm partial of panel column kk (global column k) over own rows > k; owner publishes alpha
   auto norm_partial = [&](int kk, int k) {
@@ -201,23 +202,28 @@ __global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
     }
     __syncthreads();
     norm_partial(0, k0);
+    mono_arrive(mb);
 
     // ---------------------------------------------------- panel factorization
+    // Two grid barriers per column (norm partials, then dot partials).  The
+    // next column is updated first and its norm partial published before the
+    // rest of the panel is updated, so that update overlaps the barrier.
     for (int kk = 0; kk < nbp; ++kk) {
       const int k = k0 + kk;
-      if (!grid_sync(a.gb, P)) return;
+      if (!mono_wait(mb, P)) return;
       if (warp == 0) {
         double t = 0.0;
         for (int q = lane; q < P; q += 32) t += __ldcg(pnorm + q);
         t = warp_sum(t);
         if (lane == 0) {
           const double alpha = __ldcg(alpha_slot);
-          const double xnorm = sqrt(t);
           double beta, tau, scal;
-          if (xnorm == 0.0) {
+          if (t == 0.0) {
             beta = alpha; tau = 0.0; scal = 1.0;
           } else {
-            const double h = hypot(alpha, xnorm);
+            // ||[alpha; x]|| from the sum of squares already formed (the
+            // partials overflow before this could)
+            const double h = sqrt(alpha * alpha + t);
             beta = (alpha >= 0.0) ? -h : h;
             tau = (beta - alpha) / beta;
             scal = 1.0 / (alpha - beta);
@@ -249,25 +255,30 @@ __global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
           s = warp_sum(s);
           if (lane == 0) __stcg(pdot + (size_t)p * kNB + jj, s);
         }
-        if (!grid_sync(a.gb, P)) return;
-        __shared__ double s_w[kNB];
+        if (!mono_sync(mb, P)) return;
+        __shared__ double s_w[kNB];      // tau (v^T a_jj)
         for (int jj = kk + 1 + warp; jj < nbp; jj += nwarp) {
           double s = 0.0;
           for (int q = lane; q < P; q += 32) s += __ldcg(pdot + (size_t)q * kNB + jj);
           s = warp_sum(s);
-          if (lane == 0) s_w[jj] = s;
+          if (lane == 0) s_w[jj] = tau * s;
         }
         __syncthreads();
-        if (tau != 0.0) {
-          for (int e = threadIdx.x; e < (nbp - kk - 1) * nrow; e += blockDim.x) {
-            const int jj = kk + 1 + e / nrow, i = e % nrow;
-            if (r0 + i >= k) Ps[jj * ldp + i] -= (tau * s_w[jj]) * Ps[kk * ldp + i];
-          }
-        }
+        if (tau != 0.0)
+          for (int i = threadIdx.x; i < nrow; i += blockDim.x)
+            if (r0 + i >= k) Ps[(kk + 1) * ldp + i] -= s_w[kk + 1] * Ps[kk * ldp + i];
         __syncthreads();
         norm_partial(kk + 1, k + 1);
+        mono_arrive(mb);
+        if (tau != 0.0) {
+          for (int e = threadIdx.x; e < (nbp - kk - 2) * nrow; e += blockDim.x) {
+            const int jj = kk + 2 + e / nrow, i = e % nrow;
+            if (r0 + i >= k) Ps[jj * ldp + i] -= s_w[jj] * Ps[kk * ldp + i];
+          }
+        }
       }
     }
+    __syncthreads();
 
     // ---------------------------------------------------- write back, form V
     for (int e = threadIdx.x; e < nbp * nrow; e += blockDim.x) {
@@ -328,7 +339,7 @@ __global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
         }
       }
     }
-    if (!grid_sync(a.gb, P)) return;
+    if (!mono_sync(mb, P)) return;
 
     // ---------------------------------------------------- G summed over CTAs (CTA p: entries p, p + P, ...)
     double* Gred = a.Wp + (size_t)kNB * ncols + 8;
@@ -338,7 +349,7 @@ __global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
       g = warp_sum(g);
       if (lane == 0) __stcg(Gred + e, g);
     }
-    if (!grid_sync(a.gb, P)) return;
+    if (!mono_sync(mb, P)) return;
 
     // ---------------------------------------------------- W' = T^T W
     // T^{-1} = diag(1 / tau) + striu(V^T V) (Schreiber-Van Loan T, in the
@@ -365,7 +376,7 @@ __global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
         __stcg(a.Wp + (size_t)lane * ncols + j, w * tq);
       }
     }
-    if (!grid_sync(a.gb, P)) return;
+    if (!mono_sync(mb, P)) return;
 
     // ---------------------------------------------------- C -= V W' on own rows
     // tasks (group of 32 columns, quarter h of the rows i0..nrow)

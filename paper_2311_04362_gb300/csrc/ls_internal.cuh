@@ -213,6 +213,55 @@ __device__ inline bool grid_sync(const GridBar& gb, unsigned int nblocks) {
   return s_ok != 0;
 }
 
+// Monotonic grid barrier for a cooperative launch.  The counter only grows
+// (zeroed before the launch): a CTA's e-th barrier completes when it reaches
+// e * nblocks.  Arriving is one fenced add per CTA and waiting polls with
+// acquire loads, so a barrier costs about two L2 round trips; arrive and
+// wait are separate so that a CTA can do local work while the others
+// arrive.  Waits are bounded like grid_sync's.  Every thread of every CTA
+// calls both, in the same order.
+struct MonoBar {
+  unsigned int* count;   // zero-initialised
+  unsigned int* status;
+  unsigned int epoch;
+};
+
+__device__ inline void mono_arrive(MonoBar& b) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(b.count, 1u);
+  }
+  ++b.epoch;
+}
+
+__device__ inline bool mono_wait(MonoBar& b, unsigned int nblocks) {
+  __shared__ int s_mono_ok;
+  if (threadIdx.x == 0) {
+    const unsigned int target = b.epoch * nblocks;
+    int ok = 1;
+    const uint64_t deadline = gtimer() + LS_WAIT_NS;
+    uint32_t spins = 0;
+    for (;;) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(b.count) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if ((++spins & 63u) == 0) {
+        if (gtimer() > deadline) { atomicOr(b.status, LS_DEV_TIMEOUT); ok = 0; break; }
+        if (*(volatile unsigned int*)b.status & LS_DEV_TIMEOUT) { ok = 0; break; }
+      }
+    }
+    s_mono_ok = ok;
+  }
+  __syncthreads();
+  return s_mono_ok != 0;
+}
+
+__device__ inline bool mono_sync(MonoBar& b, unsigned int nblocks) {
+  mono_arrive(b);
+  return mono_wait(b, nblocks);
+}
+
 // v with its sign flipped when bit 0 of en is set (an integer XOR on the sign
 // bit), so that acc + signed_by(v, en) is acc + v or acc - v exactly (IEEE
 // subtraction is addition of the negation) with a single FP64 add.
