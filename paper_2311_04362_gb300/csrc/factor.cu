@@ -407,6 +407,336 @@ __global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
   }
 }
 
+
+// ------------------------------------------------------------ blocked QR with lookahead
+// k_householder_la: the reflectors of k_householder_blocked, with the
+// factorization of panel p+1 overlapped with the trailing update of panel p.
+// Once W'_p is known, all warps first update panel p+1's columns on their own
+// rows; then warps 0..w-1 of every CTA factor panel p+1 (into the second
+// panel buffer, with the grid barriers of its columns) while the other warps
+// -- and the panel's once it is done -- apply panel p to the remaining
+// trailing columns, taking (32-column group, row chunk) tasks from a shared
+// counter.  w is 2 or 4 while the update is long; once it is short the
+// panel is factored by all 8 warps after the update.
+// The panel is latency-bound (two grid barriers per column) and the update
+// is FP64-bound, so the two fill each other's idle time.  Panel 0 is factored
+// by all warps.  Row dots of a panel column are summed per warp slice of the
+// rows, then over warps in warp order; CTA partials in CTA-range order.
+static constexpr int kLaTasksPerGroup = 8;
+
+__global__ void __launch_bounds__(256, 1) k_householder_la(HhArgs a) {
+  extern __shared__ double sm[];
+  __shared__ double s_tau[kNB], s_beta[kNB], s_par[3], s_w[kNB];
+  __shared__ double s_red[8][kNB];
+  __shared__ int s_bad, s_task, s_abort, s_gok;
+  const int P = gridDim.x, p = blockIdx.x;
+  const int n = a.n, ncols = n + 1;
+  const int64_t ch = (a.d + P - 1) / P;
+  const int64_t r0 = (int64_t)p * ch;
+  const int64_t r1 = min(a.d, r0 + ch);
+  const int nrow = (int)max((int64_t)0, r1 - r0);
+  const int ldp = panel_ld(ch);
+  double* pbuf0 = sm;                                 // two panel buffers, kNB columns x ldp
+  double* pbuf1 = sm + (size_t)kNB * ldp;
+  double* Gs = sm + (size_t)2 * kNB * ldp;            // W' multipliers, kNB x kNB
+  double* pnorm = a.part;                    // [P]
+  double* alpha_slot = a.part + P;           // [1]
+  double* pdot = a.part + P + 8;             // [P][kNB]
+  double* pW = pdot + (size_t)P * kNB;       // [P][kNB][ncols]
+  double* pG = pW + (size_t)P * kNB * ncols; // [P][kNB*kNB]
+  double* Gred = a.Wp + (size_t)kNB * ncols + 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* B = a.B;
+  const int64_t ldb = a.ldb;
+  MonoBar mb{a.gb.count, a.gb.status, 0u};
+  if (threadIdx.x == 0) s_abort = 0;
+
+  // the nw warps 0..nw-1 meet (all 8: the CTA barrier)
+  auto gsync = [&](int nw) {
+    if (nw == 8) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"r"(32 * nw) : "memory");
+  };
+  auto g_arrive = [&](int nw) {
+    gsync(nw);
+    if (threadIdx.x == 0) { __threadfence(); atomicAdd(mb.count, 1u); }
+    ++mb.epoch;
+  };
+  auto g_wait = [&](int nw) -> bool {
+    if (threadIdx.x == 0) {
+      const unsigned int target = mb.epoch * (unsigned int)P;
+      int ok = 1;
+      const uint64_t deadline = gtimer() + LS_WAIT_NS;
+      uint32_t spins = 0;
+      for (;;) {
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(mb.count) : "memory");
+        if ((int)(v - target) >= 0) break;
+        if ((++spins & 63u) == 0) {
+          if (gtimer() > deadline) { atomicOr(mb.status, LS_DEV_TIMEOUT); ok = 0; break; }
+          if (*(volatile unsigned int*)mb.status & LS_DEV_TIMEOUT) { ok = 0; break; }
+        }
+      }
+      s_gok = ok;
+    }
+    gsync(nw);
+    return s_gok != 0;
+  };
+  // sum over the threads of warps 0..nw-1, in warp order
+  auto gsum = [&](double v, int nw) -> double {
+    v = warp_sum(v);
+    if (lane == 0) s_red[warp][0] = v;
+    gsync(nw);
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += s_red[w][0];
+    gsync(nw);
+    return t;
+  };
+  // norm partial of column kk (global k) over own rows > k; the owner publishes alpha
+  auto norm_partial = [&](const double* Pn, int kk, int k, int nw) {
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < nrow; i += 32 * nw)
+      if (r0 + i > k) { const double v = Pn[kk * ldp + i]; ss += v * v; }
+    ss = gsum(ss, nw);
+    if (threadIdx.x == 0) {
+      __stcg(pnorm + p, ss);
+      if (k >= r0 && k < r1) __stcg(alpha_slot, Pn[kk * ldp + (k - r0)]);
+    }
+  };
+
+  // Factor the panel of columns k0 .. k0+nbp-1 (own rows) into Pn with warps
+  // 0..nw-1; the CTA's other warps do not take part.  False: rank
+  // deficiency or a timed-out barrier (status set).
+  auto factor_panel = [&](double* Pn, int k0, int nbp, int nw) -> bool {
+    const int nthr = 32 * nw;
+    for (int e = threadIdx.x; e < kNB * nrow; e += nthr) {
+      const int c = e / nrow, i = e - c * nrow;
+      Pn[c * ldp + i] = (c < nbp) ? B[(r0 + i) + (int64_t)(k0 + c) * ldb] : 0.0;
+    }
+    gsync(nw);
+    norm_partial(Pn, 0, k0, nw);
+    g_arrive(nw);
+    for (int kk = 0; kk < nbp; ++kk) {
+      const int k = k0 + kk;
+      if (!g_wait(nw)) return false;
+      if (warp == 0) {
+        double t = 0.0;
+        for (int q = lane; q < P; q += 32) t += __ldcg(pnorm + q);
+        t = warp_sum(t);
+        if (lane == 0) {
+          const double alpha = __ldcg(alpha_slot);
+          double beta, tau, scal;
+          if (t == 0.0) {
+            beta = alpha; tau = 0.0; scal = 1.0;
+          } else {
+            const double h = sqrt(alpha * alpha + t);
+            beta = (alpha >= 0.0) ? -h : h;
+            tau = (beta - alpha) / beta;
+            scal = 1.0 / (alpha - beta);
+          }
+          s_par[1] = tau; s_par[2] = scal;
+          s_tau[kk] = tau; s_beta[kk] = beta;
+          s_bad = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+        }
+      }
+      gsync(nw);
+      if (s_bad) {
+        if (p == 0 && threadIdx.x == 0) atomicOr(a.gb.status, LS_DEV_RANK);
+        return false;
+      }
+      const double tau = s_par[1], scal = s_par[2];
+      for (int i = threadIdx.x; i < nrow; i += nthr) {
+        const int64_t g = r0 + i;
+        if (g == k) Pn[kk * ldp + i] = 1.0;
+        else if (g > k && tau != 0.0) Pn[kk * ldp + i] *= scal;
+      }
+      gsync(nw);
+      if (kk + 1 < nbp) {
+        // dots v^T a_jj: lane = column jj, warp = slice of the rows >= k
+        const int i0 = (int)max((int64_t)0, (int64_t)k - r0);
+        const int len = max(0, nrow - i0);
+        const int ia = i0 + (len * warp) / nw, ib = i0 + (len * (warp + 1)) / nw;
+        const int jj = kk + 1 + lane;
+        double s = 0.0;
+        if (jj < nbp && tau != 0.0)
+          for (int i = ia; i < ib; ++i) s += Pn[kk * ldp + i] * Pn[jj * ldp + i];
+        s_red[warp][lane] = s;
+        gsync(nw);
+        if (warp == 0 && jj < nbp) {
+          double d = 0.0;
+          for (int w = 0; w < nw; ++w) d += s_red[w][lane];
+          __stcg(pdot + (size_t)p * kNB + jj, d);
+        }
+        g_arrive(nw);
+        if (!g_wait(nw)) return false;
+        // tau (v^T a_jj) summed over CTAs: warp w takes a contiguous range of CTAs
+        s = 0.0;
+        if (jj < nbp)
+          for (int q = (P * warp) / nw; q < (P * (warp + 1)) / nw; ++q) s += __ldcg(pdot + (size_t)q * kNB + jj);
+        s_red[warp][lane] = s;
+        gsync(nw);
+        if (warp == 0 && jj < nbp) {
+          double d = 0.0;
+          for (int w = 0; w < nw; ++w) d += s_red[w][lane];
+          s_w[jj] = tau * d;
+        }
+        gsync(nw);
+        if (tau != 0.0)
+          for (int i = threadIdx.x; i < nrow; i += nthr)
+            if (r0 + i >= k) Pn[(kk + 1) * ldp + i] -= s_w[kk + 1] * Pn[kk * ldp + i];
+        gsync(nw);
+        norm_partial(Pn, kk + 1, k + 1, nw);
+        g_arrive(nw);
+        if (tau != 0.0) {
+          for (int e = threadIdx.x; e < (nbp - kk - 2) * nrow; e += nthr) {
+            const int jc = kk + 2 + e / nrow, i = e % nrow;
+            if (r0 + i >= k) Pn[jc * ldp + i] -= s_w[jc] * Pn[kk * ldp + i];
+          }
+        }
+      }
+    }
+    gsync(nw);
+    return true;
+  };
+
+  // C -= V W' for column group g (of 32 from jt0) on rows [ia, ib) of own rows
+  auto update_rows = [&](const double* Ps, int jt0, int g, int ia, int ib) {
+    const int j = jt0 + 32 * g + lane;
+    if (j >= ncols || ia >= ib) return;
+    double wv[kNB];
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) wv[q] = __ldcg(a.Wp + (size_t)q * ncols + j);
+    double* cp = B + (int64_t)j * ldb + r0;
+    for (int i = ia; i < ib; ++i) {
+      double c = cp[i];
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) c -= Ps[q * ldp + i] * wv[q];
+      cp[i] = c;
+    }
+  };
+
+  if (!factor_panel(pbuf0, 0, min(kNB, n), 8)) return;
+  int cur = 0;
+  for (int k0 = 0; k0 < n; k0 += kNB) {
+    const int nbp = min(kNB, n - k0);
+    double* Ps = cur ? pbuf1 : pbuf0;
+
+    // ---------------------------------------------------- write back, form V
+    for (int e = threadIdx.x; e < nbp * nrow; e += blockDim.x) {
+      const int c = e / nrow, i = e - c * nrow;
+      const int64_t g = r0 + i;
+      const double v = Ps[c * ldp + i];
+      B[g + (int64_t)(k0 + c) * ldb] = (g == k0 + c) ? s_beta[c] : v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kNB * nrow; e += blockDim.x) {
+      const int c = e / nrow, i = e - c * nrow;
+      const int64_t g = r0 + i;
+      if (c >= nbp || g < k0 + c) Ps[c * ldp + i] = 0.0;
+      else if (g == k0 + c) Ps[c * ldp + i] = 1.0;
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------- partial G and W = V^T C (as k_householder_blocked)
+    const int i0 = (int)max((int64_t)0, (int64_t)k0 - r0);
+    for (int ls = 2 * warp; ls < 2 * warp + 2; ++ls) {
+      const int e = 32 * ls + lane;
+      if (e < kNB * (kNB - 1) / 2) {
+        int c = 1;
+        while ((c + 1) * c / 2 <= e) ++c;
+        const int r = e - c * (c - 1) / 2;
+        double g = 0.0;
+        if (c < nbp)
+          for (int i = i0; i < nrow; ++i) g += Ps[r * ldp + i] * Ps[c * ldp + i];
+        __stcg(pG + (size_t)p * kNB * kNB + e, g);
+      }
+    }
+    const int jt0 = k0 + nbp;
+    const int ngroups = (ncols - jt0 + 31) / 32;
+    {
+      const int h = warp & 3;
+      for (int g = warp >> 2; g < ngroups; g += 2) {
+        const int j = jt0 + 32 * g + lane;
+        if (j < ncols) {
+          double acc[kNB / 4];
+#pragma unroll
+          for (int q = 0; q < kNB / 4; ++q) acc[q] = 0.0;
+          const double* cp = B + (int64_t)j * ldb + r0;
+          const double* vp = Ps + (size_t)(h * (kNB / 4)) * ldp;
+#pragma unroll 2
+          for (int i = i0; i < nrow; ++i) {
+            const double c = cp[i];
+#pragma unroll
+            for (int q = 0; q < kNB / 4; ++q) acc[q] += vp[q * ldp + i] * c;
+          }
+          double* out = pW + ((size_t)p * kNB + h * (kNB / 4)) * ncols + j;
+#pragma unroll
+          for (int q = 0; q < kNB / 4; ++q) __stcg(out + (size_t)q * ncols, acc[q]);
+        }
+      }
+    }
+    if (!mono_sync(mb, P)) return;
+    for (int e = p + warp * P; e < kNB * (kNB - 1) / 2; e += 8 * P) {
+      double g = 0.0;
+      for (int q = lane; q < P; q += 32) g += __ldcg(pG + (size_t)q * kNB * kNB + e);
+      g = warp_sum(g);
+      if (lane == 0) __stcg(Gred + e, g);
+    }
+    if (!mono_sync(mb, P)) return;
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+      const int r = e / kNB, q = e - r * kNB;
+      double mv = 0.0;
+      if (r < q && q < nbp) mv = __ldcg(Gred + q * (q - 1) / 2 + r) * s_tau[r];
+      Gs[e] = mv;
+    }
+    __syncthreads();
+    {
+      const double tq = (lane < nbp) ? s_tau[lane] : 0.0;
+      for (int j = jt0 + p * 8 + warp; j < ncols; j += P * 8) {
+        double w = 0.0;
+        for (int q = 0; q < P; ++q) w += __ldcg(pW + ((size_t)q * kNB + lane) * ncols + j);
+        for (int r = 0; r + 1 < nbp; ++r) {
+          const double t = __shfl_sync(0xffffffffu, w, r);
+          if (lane > r) w = w - Gs[r * kNB + lane] * t;
+        }
+        __stcg(a.Wp + (size_t)lane * ncols + j, w * tq);
+      }
+    }
+    if (!mono_sync(mb, P)) return;
+
+    // ---------------------------------------------------- lookahead: panel p+1's columns first
+    const int len = nrow - i0;
+    if (ngroups > 0) update_rows(Ps, jt0, 0, i0 + (len * warp) / 8, i0 + (len * (warp + 1)) / 8);
+    if (threadIdx.x == 0) s_task = 0;
+    __syncthreads();
+    const int k1 = k0 + kNB;
+    const int nbp1 = (k1 < n) ? min(kNB, n - k1) : 0;
+    // warps on the next panel: few while the update is long, all of them
+    // (no overlap) once it is short (measured at d = 20,000, n = 1000: a
+    // 2-warp panel takes ~0.75 ms, an 8-warp one ~0.36 ms, the update of
+    // 31 groups ~1 ms)
+    const int grest = ngroups - 1;
+    const int nw1 = (grest >= 20) ? 2 : (grest >= 10) ? 4 : 8;
+    if (nbp1 > 0 && nw1 < 8 && warp < nw1) {
+      if (!factor_panel(cur ? pbuf0 : pbuf1, k1, nbp1, nw1) && threadIdx.x == 0) s_abort = 1;
+    }
+    // ---------------------------------------------------- the rest of C -= V W' (groups 1 ..)
+    const int ntask = (ngroups - 1) * kLaTasksPerGroup;
+    for (;;) {
+      int t = 0;
+      if (lane == 0) t = atomicAdd(&s_task, 1);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t >= ntask) break;
+      const int g = 1 + t / kLaTasksPerGroup, c = t % kLaTasksPerGroup;
+      update_rows(Ps, jt0, g, i0 + (len * c) / kLaTasksPerGroup, i0 + (len * (c + 1)) / kLaTasksPerGroup);
+    }
+    __syncthreads();
+    if (s_abort) return;
+    if (nbp1 > 0 && nw1 == 8 && !factor_panel(cur ? pbuf0 : pbuf1, k1, nbp1, 8)) return;
+    if (nbp1 > 0 && nw1 < 8 && warp >= nw1) mb.epoch += 2u * (unsigned int)nbp1 - 1u;   // the panel's grid barriers
+    cur ^= 1;
+  }
+}
+
 // ------------------------------------------------------------ prepare R
 // src: upper triangle of a column-major matrix (lds).  Writes R_out (if not
 // null, ldr), Rt[a + b*n] = R[b, a], inv_diag[i] = 1 / R[i, i].
@@ -546,6 +876,12 @@ int householder_ctas(const ls_ctx* ctx, int64_t d) {
 }
 
 static constexpr int64_t kBlockedMaxChunk = 600;   // panel slice rows per CTA in shared memory
+static constexpr int64_t kLaMaxChunk = 436;        // two panel buffers + W' multipliers in 227 KB
+
+static size_t la_smem(int64_t ch) {
+  const int64_t ldp = ch + 1 + (ch & 1);
+  return (size_t)(2 * kNB * ldp + kNB * kNB) * sizeof(double);
+}
 
 static size_t blocked_smem(int64_t ch) {
   const int64_t ldp = ch + 1 + (ch & 1);
@@ -559,6 +895,16 @@ cudaError_t launch_householder(ls_ctx* ctx, double* B, int64_t d, int64_t n, int
   cudaError_t e;
   if ((e = cudaMemsetAsync(ctx->d_status + 1, 0, 2 * sizeof(unsigned int), ctx->stream)) != cudaSuccess) return e;
   GridBar gb{ctx->d_status + 1, ctx->d_status + 2, ctx->d_status};
+  if (chunk <= kLaMaxChunk && n >= 2) {
+    const size_t smem = la_smem(chunk);
+    if ((e = cudaFuncSetAttribute(k_householder_la, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    HhArgs ha{B, d, (int)n, ldb, part, w, gb};
+    void* args[] = {&ha};
+    ++ctx->launches;
+    return cudaLaunchCooperativeKernel((const void*)k_householder_la, dim3(P), dim3(256), args, smem, ctx->stream);
+  }
   if (chunk <= kBlockedMaxChunk && n >= 2) {
     const size_t smem = blocked_smem(chunk);
     if ((e = cudaFuncSetAttribute(k_householder_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
