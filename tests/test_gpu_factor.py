@@ -43,9 +43,13 @@ def run_factor(env, Bo, seed=0):
     return host(R).reshape(n, n).T, host(x0), info
 
 
+# d = 70,000 and 100,000 give row slices of 461 and 658 per CTA on 152 SMs:
+# above the lookahead kernel's 436 (two panel buffers) and the single-buffer
+# kernel's 600, so they take the single-buffer and the unblocked kernel.
 @pytest.mark.parametrize("m,n,kappa,res,d", [(4000, 50, 1e10, 1e-6, 1000), (4000, 50, 10.0, 1e-3, 1000),
                                              (2000, 1, 1.0, 1e-2, 20), (3000, 33, 1e6, 1e-8, 660),
-                                             (20000, 257, 1e4, 1e-4, 5140), (500, 5, 1e2, 1e-1, 10)])
+                                             (20000, 257, 1e4, 1e-4, 5140), (500, 5, 1e2, 1e-1, 10),
+                                             (100000, 40, 1e6, 1e-6, 70000), (120000, 12, 1e3, 1e-4, 100000)])
 def test_factor_parity(env, m, n, kappa, res, d):
     P = problems.make_problem(m, n, kappa, res, n)
     Bo = oracle.sketch(P["A"], P["b"], d, 8, 0)

@@ -83,7 +83,7 @@ def test_fused_pass_inplace_rprev(env):
     assert host(norms)[1] == pytest.approx(np.sum((ro - rp) ** 2), rel=1e-10)
 
 
-@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 50, 64, 100, 257, 1000])
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 50, 64, 100, 257, 1000, 1025, 2048])
 def test_correct_backward_stable(env, n):
     torch, ls, ctx = env
     rng = np.random.default_rng(n)
