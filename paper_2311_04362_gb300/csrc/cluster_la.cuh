@@ -392,14 +392,32 @@ __device__ inline void ts_drain(TsSmem& sm, int n, uint64_t deadline, int& timed
     if (!mbar_wait_bounded(&sm.bar[threadIdx.x / nb][threadIdx.x % nb], 0, deadline)) timed_out = 1;
 }
 
+// For a kernel that solves more than once with buffer set sidx: wait until
+// every block of the solve that used phase `par` has landed here, then arm
+// the set's barriers for the next phase.  The caller then meets the other
+// CTAs at a cluster barrier before the next solve with this set, so no CTA
+// is still reading its entries when the next ones are pushed.  (A push for
+// the next phase may reach a barrier before it is armed: the transaction
+// count goes below zero and the phase cannot complete before the local
+// arrival, so nothing is lost.)
+__device__ inline void ts_finish(TsSmem& sm, int n, int sidx, uint32_t par, uint64_t deadline, int& timed_out) {
+  const int nb = (n + 31) / 32;
+  if ((int)threadIdx.x < nb) {
+    const int k = threadIdx.x;
+    if (!mbar_wait_bounded(&sm.bar[sidx][k], par, deadline)) timed_out = 1;
+    mbar_arrive_expect_tx(&sm.bar[sidx][k], 8u * (uint32_t)min(32, n - 32 * k));
+  }
+}
+
 // One substitution.  kBack = false: R^T y = rhs with M = R^T column-major
 // (M[i + j*ldm] = R[j, i]); kBack = true: R x = rhs with M = R.  rhs[s] is
 // read by the half-0 lane of slot s (row 32 b_s + lane); out[s] receives the
-// solution there.  sidx selects the buffers (0 first solve, 1 second).
+// solution there.  sidx selects the buffers (0 first solve, 1 second); par
+// is the barrier phase of this use of the set (ts_finish).
 template <int PP, bool kBack>
 __device__ inline void ts_solve(const CL& cl, TsSmem& sm, int sidx, const double* __restrict__ M, int64_t ldm,
                                 const double* __restrict__ inv_diag, int n, const double (&rhs)[PP],
-                                double (&out)[PP], uint64_t deadline, int& timed_out) {
+                                double (&out)[PP], uint64_t deadline, int& timed_out, uint32_t par = 0) {
   const int nb = (n + 31) / 32, P = (int)cl.ncta;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, q = w >> 1, h = w & 1;
   const int mine = ts_owned(cl, nb);
@@ -444,7 +462,7 @@ __device__ inline void ts_solve(const CL& cl, TsSmem& sm, int sidx, const double
 #pragma unroll
     for (int s = 0; s < PP; ++s) any = any || needs(s, k);
     if (any) {
-      if (!mbar_wait_bounded(&sm.bar[sidx][k], 0, deadline)) timed_out = 1;
+      if (!mbar_wait_bounded(&sm.bar[sidx][k], par, deadline)) timed_out = 1;
       double vk[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {

@@ -777,13 +777,45 @@ struct PostArgs {
   unsigned int* status;
 };
 
+template <int PP>
 __global__ void __launch_bounds__(256) k_post_factor(PostArgs a) {
+  extern __shared__ __align__(16) unsigned char ts_raw[];
+  TsSmem& sm = *reinterpret_cast<TsSmem*>(ts_raw);
   const CL cl = cl_this();
   const int n = a.n;
   const int nb = (n + 31) / 32;
+  ts_setup(cl, sm, a.R, a.ldr, a.inv_diag, n);
+  cl_sync();
+  const uint64_t deadline = gtimer() + 2000000000ull;
+  int tmo = 0;
+  uint32_t uses[2] = {0u, 0u};
+  // out = R^{-1} rhs (back) or R^{-T} rhs, both n-vectors in global memory;
+  // out is complete and visible cluster-wide on return
+  auto solve = [&](bool back, const double* rhs_g, double* out_g) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, q = w >> 1, h = w & 1;
+    const int mine = ts_owned(cl, nb);
+    double rhs[PP], out[PP];
+#pragma unroll
+    for (int s = 0; s < PP; ++s) {
+      const int o = q + 4 * s, i = 32 * ((int)cl.rank + o * (int)cl.ncta) + l;
+      rhs[s] = (h == 0 && o < mine && i < n) ? __ldcg(rhs_g + i) : 0.0;
+    }
+    const int sidx = back ? 1 : 0;
+    const uint32_t par = uses[sidx] & 1u;
+    if (back) ts_solve<PP, true>(cl, sm, 1, a.R, a.ldr, a.inv_diag, n, rhs, out, deadline, tmo, par);
+    else ts_solve<PP, false>(cl, sm, 0, a.Rt, n, a.inv_diag, n, rhs, out, deadline, tmo, par);
+#pragma unroll
+    for (int s = 0; s < PP; ++s) {
+      const int o = q + 4 * s, i = 32 * ((int)cl.rank + o * (int)cl.ncta) + l;
+      if (h == 0 && o < mine && i < n) __stcg(out_g + i, out[s]);
+    }
+    ts_finish(sm, n, sidx, par, deadline, tmo);
+    uses[sidx] += 1u;
+    cl_sync();
+  };
+
   // ---- x0 = R^{-1} z, z = (Q^T S b)[0:n] = column n of the factored B
-  cl_load_owned(cl, n, a.B + (int64_t)n * a.ldb, a.work);
-  cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, a.x0);
+  solve(true, a.B + (int64_t)n * a.ldb, a.x0);
 
   // ---- normest: power method on R^T R from a Philox start vector
   for_owned_rows(cl, n, [&](int i) { __stcg(a.v + i, power_start(a.seed, 1u, i)); });
@@ -807,7 +839,6 @@ __global__ void __launch_bounds__(256) k_post_factor(PostArgs a) {
 
   // ---- condest = ||R||_1 * Hager estimate of ||R^{-1}||_1
   double colmax = 0.0;
-  (void)nb;
   for (int b = cl.rank; b < nb; b += cl.ncta)
     for (int j = 32 * b + (int)threadIdx.x; j < min(n, 32 * b + 32); j += blockDim.x) {
       double s = 0.0;
@@ -819,8 +850,8 @@ __global__ void __launch_bounds__(256) k_post_factor(PostArgs a) {
   double* x = a.v;   // reuse
   double* y = a.w;
   for_owned_rows(cl, n, [&](int i) { __stcg(a.work + i, 1.0 / (double)n); });
-  __syncthreads();
-  cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, y);      // y = R^{-1} x
+  cl_sync();
+  solve(true, a.work, y);                                    // y = R^{-1} x
   double est;
   if (n == 1) {
     est = fabs(__ldcg(y));
@@ -828,14 +859,13 @@ __global__ void __launch_bounds__(256) k_post_factor(PostArgs a) {
     est = cl_norm1(cl, n, y, a.slots);
     for_owned_rows(cl, n, [&](int i) { __stcg(a.xi + i, sgn1(__ldcg(y + i))); });
     cl_sync();
-    cl_load_owned(cl, n, a.xi, a.work);
-    cl_solve_RT(cl, a.Rt, n, a.inv_diag, a.work, x);         // x = R^{-T} xi
+    solve(false, a.xi, x);                                   // x = R^{-T} xi
     int j = cl_argmax_abs(cl, n, x, a.slots);
     int iter = 2;
     for (;;) {
       for_owned_rows(cl, n, [&](int i) { __stcg(a.work + i, i == j ? 1.0 : 0.0); });
-      __syncthreads();
-      cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, y);  // y = R^{-1} e_j
+      cl_sync();
+      solve(true, a.work, y);                                // y = R^{-1} e_j
       const double est_old = est;
       est = cl_norm1(cl, n, y, a.slots);
       double diff = 0.0;
@@ -844,8 +874,7 @@ __global__ void __launch_bounds__(256) k_post_factor(PostArgs a) {
       if (any_diff == 0.0 || est <= est_old) break;
       for_owned_rows(cl, n, [&](int i) { __stcg(a.xi + i, sgn1(__ldcg(y + i))); });
       cl_sync();
-      cl_load_owned(cl, n, a.xi, a.work);
-      cl_solve_RT(cl, a.Rt, n, a.inv_diag, a.work, x);       // x = R^{-T} xi
+      solve(false, a.xi, x);                                 // x = R^{-T} xi
       const int jlast = j;
       j = cl_argmax_abs(cl, n, x, a.slots);
       if (__ldcg(x + jlast) != fabs(__ldcg(x + j)) && iter < 5) { iter += 1; continue; }
@@ -855,12 +884,13 @@ __global__ void __launch_bounds__(256) k_post_factor(PostArgs a) {
       const double v = 1.0 + (double)i / (double)(n - 1);
       __stcg(a.work + i, (i % 2 == 0) ? v : -v);
     });
-    __syncthreads();
-    cl_solve_R(cl, a.R, a.ldr, n, a.inv_diag, a.work, y);
+    cl_sync();
+    solve(true, a.work, y);
     double alt = cl_norm1(cl, n, y, a.slots);
     alt = 2.0 * alt / (3.0 * (double)n);
     if (alt > est) est = alt;
   }
+  if (tmo) atomicOr(a.status, LS_DEV_TIMEOUT);
   if (cl.rank == 0 && threadIdx.x == 0) {
     a.est[0] = normest;
     a.est[1] = norm1 * est;
@@ -957,13 +987,33 @@ cudaError_t launch_post_factor(ls_ctx* ctx, const double* B, int64_t d, int64_t 
                                int64_t ldr, double* x0, uint64_t seed, const double* Rt, const double* inv_diag,
                                double* vecs /* 4n + 64 */, double* est_out) {
   (void)d;
+  static int P = -1;
+  if (P < 0) {
+    const void* fns[] = {(const void*)k_post_factor<1>, (const void*)k_post_factor<2>};
+    P = ts_cluster_size_of(fns, 2);
+  }
+  const int pp = ts_slots((int)n, P);
+  if (pp == 0 || n > kTsMaxN) return cudaErrorInvalidValue;
   PostArgs a;
   a.B = B; a.ldb = ldb; a.n = (int)n; a.R = R; a.ldr = ldr; a.Rt = Rt; a.inv_diag = inv_diag;
   a.x0 = x0; a.seed = seed;
   a.v = vecs; a.w = vecs + n; a.xi = vecs + 2 * n; a.work = vecs + 3 * n; a.slots = vecs + 4 * n;
   a.est = est_out; a.status = ctx->d_status;
   void* args[] = {&a};
-  return launch_cluster(ctx, (const void*)k_post_factor, args, ctx->cluster);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = sizeof(TsSmem);
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++ctx->launches;
+  return cudaLaunchKernelExC(&cfg, pp == 1 ? (const void*)k_post_factor<1> : (const void*)k_post_factor<2>, args);
 }
 
 }  // namespace lsk

@@ -659,17 +659,14 @@ cudaError_t launch_reduce_partials(ls_ctx* ctx, const double* part, int nparts, 
   return cudaGetLastError();
 }
 
-// Cluster size for the broadcast substitutions: 16 CTAs where the device
-// can hold such a cluster with the solve's shared memory, else 8.
-int ts_cluster_size() {
-  static int size = -1;
-  if (size > 0) return size;
-  const void* fns[] = {(const void*)k_iter_step<1>, (const void*)k_iter_step<2>, (const void*)k_correct<1>,
-                       (const void*)k_correct<2>};
+// Cluster size for kernels built on the broadcast substitutions: 16 CTAs
+// where the device can hold such a cluster of every listed kernel with the
+// solves' shared memory (TsSmem), else 8.  Sets the kernels' attributes.
+int ts_cluster_size_of(const void* const* fns, int nfn) {
   bool ok16 = true;
-  for (const void* f : fns) {
-    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TsSmem));
-    if (cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) ok16 = false;
+  for (int f = 0; f < nfn; ++f) {
+    cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TsSmem));
+    if (cudaFuncSetAttribute(fns[f], cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) ok16 = false;
   }
   cudaGetLastError();
   if (ok16) {
@@ -685,11 +682,19 @@ int ts_cluster_size() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    for (const void* f : fns)
-      if (cudaOccupancyMaxActiveClusters(&nclusters, f, &cfg) != cudaSuccess || nclusters < 1) ok16 = false;
+    for (int f = 0; f < nfn; ++f)
+      if (cudaOccupancyMaxActiveClusters(&nclusters, fns[f], &cfg) != cudaSuccess || nclusters < 1) ok16 = false;
     cudaGetLastError();
   }
-  size = ok16 ? 16 : 8;
+  return ok16 ? 16 : 8;
+}
+
+int ts_cluster_size() {
+  static int size = -1;
+  if (size > 0) return size;
+  const void* fns[] = {(const void*)k_iter_step<1>, (const void*)k_iter_step<2>, (const void*)k_correct<1>,
+                       (const void*)k_correct<2>};
+  size = ts_cluster_size_of(fns, 4);
   return size;
 }
 

@@ -433,6 +433,7 @@ struct StepArgs {
   double* y_out; double* d_out;
 };
 cudaError_t launch_iter_step(ls_ctx* ctx, const StepArgs& a);
+int ts_cluster_size_of(const void* const* fns, int nfn);
 
 // sparse A (sparse.cu)
 size_t sp_gather_smem(int64_t n);
