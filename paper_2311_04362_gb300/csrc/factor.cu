@@ -3,6 +3,12 @@
 // x0 = R^{-1} (Q^T S b) (Sec. 2.3, Eq. (2.5)) and the two estimates of the
 // Sec. 3.3 stopping rule.
 //
+// Three QR kernels, chosen by the rows per CTA (ch = ceil(d / P)):
+//   k_householder_la (ch <= 436): blocked compact-WY with one panel of
+//     lookahead (two panel buffers in shared memory);
+//   k_householder_blocked (ch <= 600): the same steps, one panel buffer;
+//   k_householder (taller slices): unblocked, described next.
+//
 // k_householder: one cooperative launch, P CTAs, each owning a contiguous
 // slice of the d rows.  Column k is reduced with three bounded grid barriers:
 //   1. partial sums of squares of column k below the diagonal  -> barrier
@@ -17,9 +23,10 @@
 // k_prepare_R: R (upper, strictly-lower part zeroed), its transpose Rt and
 // the reciprocal diagonal used by every later substitution.
 //
-// k_post_factor: one thread-block cluster.  Solves R x0 = (Q^T S b)[0:n],
-// runs ceil(ln n) power steps on R (normest) and Hager's 1-norm estimator of
-// ||R^{-1}||_1 times ||R||_1 (condest).
+// k_post_factor: one thread-block cluster (16 CTAs where they fit).  Solves
+// R x0 = (Q^T S b)[0:n], runs ceil(ln n) power steps on R (normest) and
+// Hager's 1-norm estimator of ||R^{-1}||_1 times ||R||_1 (condest); the
+// substitutions are the broadcast ones of cluster_la.cuh.
 #include <algorithm>
 
 #include "cluster_la.cuh"
