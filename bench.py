@@ -192,7 +192,7 @@ def main():
     ap.add_argument("--check-qr", action="store_true", help="also compute the Householder-QR forward error (slow)")
     ap.add_argument("--count", type=int, default=None, help="problems for --case batched / serve")
     ap.add_argument("--q", type=int, default=None, help="iterations for --case batched (stopping rule off)")
-    ap.add_argument("--case", choices=["solve", "pass", "sketch", "batched", "serve"], default="solve",
+    ap.add_argument("--case", choices=["solve", "pass", "sketch", "factor", "batched", "serve"], default="solve",
                     help="pass / sketch: only the fused residual/gradient pass, or only the sketch B = S[A b], "
                          "on an m x 1000 problem (for ncu captures)")
     ap.add_argument("--m", type=int, default=200_000, help="rows for --case pass")
@@ -211,6 +211,8 @@ def main():
         return reference_arm(args, world, rank)
     if args.case == "pass":
         return pass_case(args)
+    if args.case == "factor":
+        return factor_case(args)
     if args.case == "sketch":
         return sketch_case(args)
     if args.case == "batched":
@@ -779,6 +781,43 @@ def sketch_case(args):
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"case": "sketch", "m": m, "n": n, "d": d, "zeta": zeta, "ms_per_call": ms,
                       "alg_gbs": (8.0 * m * (n + 1) + 8.0 * d * (n + 1)) / (ms / 1e3) / 1e9}))
+
+
+def factor_case(args):
+    """The factor step alone (ls_factor: Householder QR, start x0, estimates)
+    on a d x (n + 1) column-major matrix of the large workload's sketch shape
+    (d = 20,000, n = --n, default 1000: 160 MB), timed with CUDA events on the
+    launching stream; B is restored from a copy before each call (the copy is
+    outside the timed interval).  Used for small-case ncu captures of the QR."""
+    import torch
+
+    import paper_2311_04362_gb300 as ls
+    from paper_2311_04362_gb300 import build
+
+    build.build()
+    n = args.n
+    d = 20 * n
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    B0 = torch.randn((n + 1) * d, dtype=torch.float64, device="cuda", generator=g)
+    B = torch.empty_like(B0)
+    R = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    x0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    times = []
+    with ls.Context(0, stream) as ctx:
+        for it in range(args.warmup + args.steps):
+            B.copy_(B0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.ls_factor(B, d, n, d, R, n, x0, 0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    flops = 2.0 * d * (n + 1) ** 2 - 2.0 / 3.0 * (n + 1) ** 3
+    print(json.dumps({"case": "factor", "d": d, "n": n, "ms_per_call": ms, "qr_tflops": flops / (ms / 1e3) / 1e12}))
 
 
 def reference_arm(args, world, rank):
