@@ -142,20 +142,20 @@ __global__ void __launch_bounds__(256) k_gather_add(const double* __restrict__ A
     const int64_t e0 = row_ptr[t], e1 = row_ptr[t + 1];
     double a0 = 0.0, a1 = 0.0;
     int64_t e = e0;
-    for (; e + 4 <= e1; e += 4) {
-      uint32_t en[4];
-      double2 v[4];
+    for (; e + 8 <= e1; e += 8) {
+      uint32_t en[8];
+      double2 v[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) en[u] = __ldg(ent + e + u);
+      for (int u = 0; u < 8; ++u) en[u] = __ldg(ent + e + u);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const double* p = A + (int64_t)(en[u] >> 1) * lda + c;
         if (pair) v[u] = __ldg(reinterpret_cast<const double2*>(p));
         else if (single) { v[u].x = __ldg(p); v[u].y = 0.0; }
         else { v[u].x = 0.0; v[u].y = 0.0; }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         a0 = a0 + signed_by(v[u].x, en[u]);
         a1 = a1 + signed_by(v[u].y, en[u]);
       }
