@@ -150,6 +150,7 @@ constexpr int64_t kMaxN = 2048;   // fused pass keeps up to 8 columns per thread
 // scratch layouts ---------------------------------------------------------------
 struct SketchScratch {
   int32_t* rows; uint32_t* signs; int64_t* row_ptr; uint32_t* ent; unsigned long long* fill;
+  int64_t* split;   // entry offsets of the upload pieces, d * (kMaxPieces + 1)
 };
 SketchScratch carve_sketch(Carve& c, int64_t m, int64_t d, int zeta) {
   SketchScratch s;
@@ -158,6 +159,7 @@ SketchScratch carve_sketch(Carve& c, int64_t m, int64_t d, int zeta) {
   s.row_ptr = c.take<int64_t>((size_t)d + 1);
   s.ent = c.take<uint32_t>((size_t)m * zeta);
   s.fill = c.take<unsigned long long>((size_t)d);
+  s.split = c.take<int64_t>((size_t)d * (kMaxPieces + 1));
   return s;
 }
 
@@ -268,6 +270,7 @@ ls_status ls_destroy(ls_ctx* ctx) {
   if (ctx->d_misc) cudaFree(ctx->d_misc);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
+  for (auto& e : ctx->piece_done) if (e) cudaEventDestroy(e);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   for (auto& e : ctx->ev) if (e) cudaEventDestroy(e);
   for (auto& e : ctx->pass_ev) if (e) cudaEventDestroy(e);
@@ -356,17 +359,35 @@ ls_status ls_sketch_csr(ls_ctx* ctx, int64_t m, int64_t d, int zeta, const int32
   return sync_and_check(ctx);
 }
 
+// Host A uploaded in row pieces: piece i (rows bnd.r[i] .. bnd.r[i+1]) may be
+// read after event ev[i].
+struct UploadPieces {
+  int np;
+  PieceBounds bnd;
+  cudaEvent_t ev[kMaxPieces];
+};
+
 // wait_A (may be null): an event after which A may be read (an upload in
 // flight); the indices and the CSR, which do not read A, run before it.
 static ls_status sketch_impl(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                              int64_t d, int zeta, uint64_t seed, double* B, int64_t ldb, Carve& cc,
-                             cudaEvent_t wait_A = nullptr) {
+                             cudaEvent_t wait_A = nullptr, const UploadPieces* up = nullptr) {
   SketchScratch s = carve_sketch(cc, m, d, zeta);
   CUDA_TRY(ctx, launch_sketch_indices(ctx, m, d, zeta, seed, s.rows, s.signs));
   ls_status st = sketch_csr_impl(ctx, m, d, zeta, s.rows, s.signs, s.row_ptr, s.ent, s.fill);
   if (st) return st;
-  if (wait_A) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, wait_A, 0));
   const double scale = 1.0 / std::sqrt((double)zeta);
+  if (up) {
+    // gather each piece of A as it lands; the running sums continue in B
+    CUDA_TRY(ctx, launch_sketch_split(ctx, d, s.row_ptr, s.ent, up->np, up->bnd, s.split));
+    CUDA_TRY(ctx, launch_sketch_gather_b(ctx, b, d, s.row_ptr, s.ent, scale, B + n * ldb));
+    for (int i = 0; i < up->np; ++i) {
+      CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, up->ev[i], 0));
+      CUDA_TRY(ctx, launch_sketch_gather_piece(ctx, A, n, lda, d, s.split, up->np, i, s.ent, scale, B, ldb));
+    }
+    return LS_OK;
+  }
+  if (wait_A) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, wait_A, 0));
   CUDA_TRY(ctx, launch_sketch_apply(ctx, A, m, n, lda, b, d, s.row_ptr, s.ent, scale, B, ldb));
   return LS_OK;
 }
@@ -1083,23 +1104,31 @@ ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int64_t m, 
     bd = p;
   }
   cudaEvent_t wait_A = nullptr;
+  UploadPieces pieces{};
   if (!dA) {
     // upload A on the copy stream in a few large pieces (one 16 GB copy
     // measured ~30% slower than four), overlapping the sketch's indices and
-    // CSR; the gather waits for the upload
+    // CSR; the gather takes each piece as it lands
     if (!ctx->copy_stream) {
       CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
       CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming));
+      for (auto& e : ctx->piece_done) CUDA_TRY(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     double* p = sc.take<double>((size_t)m * lda);
     CUDA_TRY(ctx, cudaEventRecord(ctx->copy_done, ctx->stream));      // after earlier work on the stream
     CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_done, 0));
-    const int64_t pieces = 4, rows = (m + pieces - 1) / pieces;
+    const int64_t rows = (m + kMaxPieces - 1) / kMaxPieces;
+    pieces.np = 0;
     for (int64_t r0 = 0; r0 < m; r0 += rows) {
       const int64_t nr = std::min(rows, m - r0);
       CUDA_TRY(ctx, cudaMemcpyAsync(p + r0 * lda, A + r0 * lda, sizeof(double) * (size_t)nr * lda,
                                     cudaMemcpyHostToDevice, ctx->copy_stream));
+      CUDA_TRY(ctx, cudaEventRecord(ctx->piece_done[pieces.np], ctx->copy_stream));
+      pieces.bnd.r[pieces.np] = r0;
+      pieces.ev[pieces.np] = ctx->piece_done[pieces.np];
+      ++pieces.np;
     }
+    pieces.bnd.r[pieces.np] = m;
     CUDA_TRY(ctx, cudaEventRecord(ctx->copy_done, ctx->copy_stream));
     wait_A = ctx->copy_done;
     Ad = p;
@@ -1129,7 +1158,8 @@ ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int64_t m, 
 
   const long long l0 = ctx->launches;
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
-  if ((st = sketch_impl(ctx, Ad, m, n, lda, bd, d, zeta, seed, B, d, cc, wait_A))) return st;
+  if ((st = sketch_impl(ctx, Ad, m, n, lda, bd, d, zeta, seed, B, d, cc, wait_A, dA ? nullptr : &pieces)))
+    return st;
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
   cc.off = mark2;
   double est[2];

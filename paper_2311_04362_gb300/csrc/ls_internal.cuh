@@ -356,6 +356,7 @@ struct ls_ctx {
   // sketch's indices and CSR (which do not read A) run on `stream`
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_done = nullptr;
+  cudaEvent_t piece_done[4] = {nullptr, nullptr, nullptr, nullptr};   // host A uploaded piece by piece
 };
 
 // ------------------------------------------------------------ launch helpers
@@ -374,6 +375,17 @@ int sketch_sort_cap();
 cudaError_t launch_sketch_apply(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda,
                                 const double* b, int64_t d, const int64_t* row_ptr,
                                 const uint32_t* ent, double scale, double* B, int64_t ldb);
+// Gather by row pieces of A (as they are uploaded): bounds[0] = 0 <
+// bounds[1] < ... < bounds[np] = m; split gets d * (np + 1) entry offsets.
+constexpr int kMaxPieces = 4;
+struct PieceBounds { int64_t r[kMaxPieces + 1]; };
+cudaError_t launch_sketch_split(ls_ctx* ctx, int64_t d, const int64_t* row_ptr, const uint32_t* ent, int np,
+                                const PieceBounds& bnd, int64_t* split);
+cudaError_t launch_sketch_gather_b(ls_ctx* ctx, const double* b, int64_t d, const int64_t* row_ptr,
+                                   const uint32_t* ent, double scale, double* Bcol);
+cudaError_t launch_sketch_gather_piece(ls_ctx* ctx, const double* A, int64_t n, int64_t lda, int64_t d,
+                                       const int64_t* split, int np, int piece, const uint32_t* ent, double scale,
+                                       double* B, int64_t ldb);
 
 int householder_ctas(const ls_ctx* ctx, int64_t d);
 size_t householder_part_doubles(const ls_ctx* ctx, int64_t d, int64_t n);

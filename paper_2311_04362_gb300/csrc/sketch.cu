@@ -129,18 +129,35 @@ __global__ void __launch_bounds__(256) k_bucket_sort(int64_t d, const int64_t* _
 // ---------------------------------------------------------------- (a3)
 // CTA tile: 32 sketch rows x 64 columns of A; warp w owns rows 4w..4w+3 of
 // the tile, lane l owns columns 2l, 2l+1 (one 16-byte load per bucket entry).
+// With split != null only the entries of row piece `piece` of np are added:
+// each bucket's running sum is kept unscaled in B between pieces (piece 0
+// starts from 0, later pieces continue it) and the last piece applies the
+// scale, so the sums and their order, and B, are those of one launch.
 __global__ void __launch_bounds__(256) k_gather_add(const double* __restrict__ A, int64_t lda, int64_t n, int64_t d,
                                                     const int64_t* __restrict__ row_ptr,
                                                     const uint32_t* __restrict__ ent, double scale,
-                                                    double* __restrict__ B, int64_t ldb) {
+                                                    double* __restrict__ B, int64_t ldb,
+                                                    const int64_t* __restrict__ split, int np, int piece) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c = (int64_t)blockIdx.y * 64 + 2 * lane;
   const bool pair = (c + 1 < n), single = (c < n);
+  const bool first = (split == nullptr) || piece == 0, last = (split == nullptr) || piece == np - 1;
   for (int tt = 0; tt < 4; ++tt) {
     const int64_t t = (int64_t)blockIdx.x * 32 + warp * 4 + tt;
     if (t >= d) break;
-    const int64_t e0 = row_ptr[t], e1 = row_ptr[t + 1];
+    int64_t e0, e1;
+    if (split) {
+      e0 = split[t * (np + 1) + piece];
+      e1 = split[t * (np + 1) + piece + 1];
+    } else {
+      e0 = row_ptr[t];
+      e1 = row_ptr[t + 1];
+    }
     double a0 = 0.0, a1 = 0.0;
+    if (!first) {
+      if (single) a0 = B[t + c * ldb];
+      if (pair) a1 = B[t + (c + 1) * ldb];
+    }
     int64_t e = e0;
     for (; e + 8 <= e1; e += 8) {
       uint32_t en[8];
@@ -169,8 +186,28 @@ __global__ void __launch_bounds__(256) k_gather_add(const double* __restrict__ A
       a0 = a0 + signed_by(v.x, en);
       a1 = a1 + signed_by(v.y, en);
     }
-    if (single) B[t + c * ldb] = scale * a0;
-    if (pair) B[t + (c + 1) * ldb] = scale * a1;
+    if (single) B[t + c * ldb] = last ? scale * a0 : a0;
+    if (pair) B[t + (c + 1) * ldb] = last ? scale * a1 : a1;
+  }
+}
+
+// split[t * (np + 1) + i] = the first entry of bucket t whose row is >=
+// bnd.r[i] (a bucket's entries ascend by row; entry = row << 1 | sign).
+__global__ void k_split_entries(int64_t d, const int64_t* __restrict__ row_ptr, const uint32_t* __restrict__ ent,
+                                int np, PieceBounds bnd, int64_t* __restrict__ split) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d) return;
+  const int64_t e0 = row_ptr[t], e1 = row_ptr[t + 1];
+  split[t * (np + 1)] = e0;
+  split[t * (np + 1) + np] = e1;
+  for (int i = 1; i < np; ++i) {
+    int64_t lo = e0, hi = e1;                       // first entry with row >= bnd.r[i]
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if ((int64_t)(__ldg(ent + mid) >> 1) < bnd.r[i]) lo = mid + 1;
+      else hi = mid;
+    }
+    split[t * (np + 1) + i] = lo;
   }
 }
 
@@ -241,10 +278,34 @@ cudaError_t launch_sketch_apply(ls_ctx* ctx, const double* A, int64_t m, int64_t
   (void)m;
   cudaError_t e;
   dim3 grid((unsigned)((d + 31) / 32), (unsigned)((n + 63) / 64));
-  k_gather_add<<<grid, 256, 0, ctx->stream>>>(A, lda, n, d, row_ptr, ent, scale, B, ldb);
+  k_gather_add<<<grid, 256, 0, ctx->stream>>>(A, lda, n, d, row_ptr, ent, scale, B, ldb, nullptr, 1, 0);
   ++ctx->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_gather_b<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(b, d, row_ptr, ent, scale, B + n * ldb);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_split(ls_ctx* ctx, int64_t d, const int64_t* row_ptr, const uint32_t* ent, int np,
+                                const PieceBounds& bnd, int64_t* split) {
+  if (np < 1 || np > kMaxPieces) return cudaErrorInvalidValue;
+  k_split_entries<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(d, row_ptr, ent, np, bnd, split);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_gather_b(ls_ctx* ctx, const double* b, int64_t d, const int64_t* row_ptr,
+                                   const uint32_t* ent, double scale, double* Bcol) {
+  k_gather_b<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(b, d, row_ptr, ent, scale, Bcol);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_gather_piece(ls_ctx* ctx, const double* A, int64_t n, int64_t lda, int64_t d,
+                                       const int64_t* split, int np, int piece, const uint32_t* ent, double scale,
+                                       double* B, int64_t ldb) {
+  dim3 grid((unsigned)((d + 31) / 32), (unsigned)((n + 63) / 64));
+  k_gather_add<<<grid, 256, 0, ctx->stream>>>(A, lda, n, d, nullptr, ent, scale, B, ldb, split, np, piece);
   ++ctx->launches;
   return cudaGetLastError();
 }
