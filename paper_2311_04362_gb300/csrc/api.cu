@@ -255,7 +255,6 @@ ls_status ls_create(ls_ctx** out, int device, void* cuda_stream) {
   }
   cudaMemset(ctx->d_status, 0, 16 * sizeof(unsigned int));
   for (auto& e : ctx->ev) cudaEventCreate(&e);
-  ctx->cluster = 8;
   *out = ctx;
   return LS_OK;
 }

@@ -973,23 +973,6 @@ size_t householder_part_doubles(const ls_ctx* ctx, int64_t d, int64_t n) {
 
 size_t householder_w_doubles(int64_t n) { return (size_t)kNB * (size_t)(n + 1) + 8 + kNB * kNB; }
 
-cudaError_t launch_cluster(ls_ctx* ctx, const void* fn, void** args, int cluster) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cluster);
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  ++ctx->launches;
-  return cudaLaunchKernelExC(&cfg, fn, args);
-}
-
 cudaError_t launch_post_factor(ls_ctx* ctx, const double* B, int64_t d, int64_t n, int64_t ldb, const double* R,
                                int64_t ldr, double* x0, uint64_t seed, const double* Rt, const double* inv_diag,
                                double* vecs /* 4n + 64 */, double* est_out) {

@@ -346,8 +346,6 @@ struct ls_ctx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> pass_ev;    // two per fused-pass launch of ls_iterate
   long long launches = 0;              // kernels launched (for ls_info)
-  // cluster size used by the small dense kernels
-  int cluster = 8;
   // TMA encode entry point
   void* encode_tiled = nullptr;
   // batched pass geometry (ls_tune_batched)
@@ -398,7 +396,6 @@ cudaError_t launch_post_factor(ls_ctx* ctx, const double* B, int64_t d, int64_t 
                                const double* R, int64_t ldr, double* x0, uint64_t seed,
                                const double* Rt, const double* inv_diag, double* vecs /* 4n+64 */,
                                double* est_out /* 2 */);
-cudaError_t launch_cluster(ls_ctx* ctx, const void* fn, void** args, int cluster);
 
 // Iteration state on the device.
 struct IterState {
