@@ -106,3 +106,19 @@ def test_api_rejects_without_a_context(libpath):
     assert L.ls_solve_sparse(None, None, None, None, 10, 2, 20, None, 4, 8, 10, 0, None, None, None) == ls.LS_EINVAL
     n_out = C.c_int()
     assert L.ls_server_poll(None, None, None, 0, C.byref(n_out)) == ls.LS_EINVAL
+
+
+def test_workspace_bytes_covers_the_solve(libpath):
+    """ls_workspace_bytes (no GPU here: the host path assumes 152 SMs) is 0 for
+    an invalid shape, grows with every dimension, and covers at least the
+    arrays a solve of that shape must hold at once: the sketch B_aug (d x
+    (n+1) doubles) and R (n x n) beside the sketch's bucket entries (m zeta
+    4-byte words, twice: the hash output and the sorted CSR)."""
+    import paper_2311_04362_gb300 as ls
+    L = ls.lib()
+    assert L.ls_workspace_bytes(0, 10, 20, 8) == 0 and L.ls_workspace_bytes(100, 10, 20, 0) == 0
+    m, n, d, z = 200_000, 100, 2000, 8
+    w = L.ls_workspace_bytes(m, n, d, z)
+    assert w >= 8 * d * (n + 1) + 8 * n * n + 2 * 4 * m * z
+    for args in [(2 * m, n, d, z), (m, 2 * n, 2 * d, z), (m, n, 2 * d, z), (m, n, d, 2 * z)]:
+        assert L.ls_workspace_bytes(*args) >= w, args
