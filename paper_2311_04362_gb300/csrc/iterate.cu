@@ -13,9 +13,12 @@
 // over CTAs in index order by the next kernel, so results are bit-identical
 // run to run.  Every wait is bounded by %globaltimer.
 //
-// k_iter_step / k_correct (a7): one thread-block cluster sums the partials,
-// applies the stopping rule and performs the two triangular solves
-// (cluster_la.cuh) and the update.
+// k_fused_pass_ws: the warp-specialized form for n > 256 (below).
+//
+// k_iter_step / k_correct (a7): one thread-block cluster (16 CTAs where they
+// fit) sums the partials, applies the stopping rule and performs the two
+// triangular solves (the broadcast substitutions of cluster_la.cuh) and the
+// update.
 #include "cluster_la.cuh"
 
 namespace lsk {
@@ -247,17 +250,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_fused_pass(const __grid_constan
   (void)s_abort;
 }
 
-// k_fused_pass_ws: the same pass for n > 256 (tr = 8 or 4), warp-specialized
-// so that the FP64 pipe does not idle at block-wide barriers between the two
-// uses of a tile.  Warps 0-3 (row group) form the row dots of tile k -- lane
-// (r, q) of warp w sums the columns c = LPR ((w + r) mod 4) + q (mod 4 LPR),
-// LPR = 32 / tr -- combine them (two shuffles, then the 4 warps in warp order
-// by one thread per row), form r_j and the norms, and hand r to the column
-// group through an mbarrier; warps 4-7 (column group) add r_j A_jk to their
-// columns for tile k while the row group is already on tile k + 1.  The r
-// buffer and the row-dot partials are double-buffered; the column group
-// releases a tile's stage and its r buffer.  Same arithmetic as the phases of
-// k_fused_pass (and the same deterministic orders within a CTA).
+// k_fused_pass_ws: the same pass for n > 256 (tr = 16, 8 or 4), warp-
+// specialized so that the FP64 pipe does not idle at block-wide barriers
+// between the two uses of a tile.  Warps 0-3 (row group) form the row dots of
+// tile k -- lane (r, q) of warp w sums the columns c = LPR ((w + r) mod 4) + q
+// (mod 4 LPR), LPR = 32 / tr, in two interleaved chains -- combine them (two
+// shuffles, then the 4 warps in warp order by one thread per row), form r_j
+// and the norms, and hand r to the column group through an mbarrier; warps
+// 4-7 (column group) add r_j A_jk to their columns for tile k while the row
+// group runs ahead.  r has one buffer per tile stage (so the row group may be
+// up to S - 1 tiles ahead) and the row-dot partials two; the column group
+// releases a tile's stage and its r buffer.  Deterministic orders within a
+// CTA, as in k_fused_pass.
 template <int NPT2>
 __global__ void __launch_bounds__(kThreads, 1) k_fused_pass_ws(const __grid_constant__ CUtensorMap map, PassArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
