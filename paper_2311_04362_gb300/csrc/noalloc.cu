@@ -7,6 +7,7 @@
 // a file-scope __device__ array of fixed size, so the call allocates nothing:
 // every GPU that loads this library keeps kNoAllocBytes of it until the
 // process exits.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -24,26 +25,31 @@ constexpr size_t kNoAllocBytes = kPartDoubles * sizeof(double) + 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of g_noalloc_scratch per device (host code may not use the
-// symbol itself as a device pointer: on the host it is only a stand-in).
+// symbol itself as a device pointer: on the host it is only a stand-in), with
+// the device's SM count and compute capability, looked up once per device.
 void* g_scratch_addr[kNoAllocMaxDevices] = {nullptr};
 int g_num_sms[kNoAllocMaxDevices] = {0};
+int g_cc[kNoAllocMaxDevices] = {0};     // 10 * major + minor
 std::mutex g_setup_mu;
 
-cudaError_t scratch_for_device(int dev, void** out, int* num_sms) {
+cudaError_t scratch_for_device(int dev, void** out, int* num_sms, int* cc) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // device `dev` is current
     if (e != cudaSuccess) return e;
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
+    int sms = 0, major = 0, minor = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev)) != cudaSuccess) return e;
     g_num_sms[dev] = sms;
+    g_cc[dev] = 10 * major + minor;
+    g_scratch_addr[dev] = p;
   }
   *out = g_scratch_addr[dev];
   *num_sms = g_num_sms[dev];
+  *cc = g_cc[dev];
   return cudaSuccess;
 }
 
@@ -59,12 +65,10 @@ extern "C" LS_API ls_status ls_residual_gradient_noalloc(void* cuda_stream, cons
   if (lda < n || (lda & 1) || (reinterpret_cast<uintptr_t>(A) & 15)) return LS_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return LS_ECUDA;
-  cudaDeviceProp prop;
-  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return LS_ECUDA;
-  if (prop.major != 10 || prop.minor != 3) return LS_ECUDA;
   void* scratch = nullptr;
-  int sms = 0;
-  if (scratch_for_device(dev, &scratch, &sms) != cudaSuccess) return LS_ECUDA;
+  int sms = 0, cc = 0;
+  if (scratch_for_device(dev, &scratch, &sms, &cc) != cudaSuccess) return LS_ECUDA;
+  if (cc != 103) return LS_ECUDA;                                 // built for sm_103a only
 
   // A context on the stack: only what the launch helpers read (no allocation).
   ls_ctx ctx;
@@ -75,7 +79,9 @@ extern "C" LS_API ls_status ls_residual_gradient_noalloc(void* cuda_stream, cons
   ctx.d_status = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(scratch) + kPartDoubles * sizeof(double));
 
   lsk::PassGeom g = lsk::pass_geometry(&ctx, n, m);
-  if (g.grid > kNoAllocMaxCtas) return LS_EINVAL;
+  // the pass walks its tiles with a grid stride, so fewer CTAs than SMs is
+  // still correct; the partial count below follows g.grid
+  g.grid = std::min(g.grid, kNoAllocMaxCtas);
   CUtensorMap map;
   if (lsk::make_tensor_map(&ctx, &map, A, m, n, lda, g) != cudaSuccess) return LS_ECUDA;
   // the status words must start at zero; the partials are fully overwritten
