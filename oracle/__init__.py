@@ -233,6 +233,60 @@ def residual_gradient(A, b, x):
     return r, c
 
 
+def _veltkamp(a):
+    """a = hi + lo exactly, hi with at most 26 significant bits (Veltkamp's
+    splitting with the constant 2^27 + 1; no overflow for |a| < 2^996)."""
+    c = 134217729.0 * a
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def two_product(a, b):
+    """p + e = a b exactly (Dekker's product from the splitting above), for
+    FP64 arrays whose products neither overflow nor underflow."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    p = a * b
+    ah, al = _veltkamp(a)
+    bh, bl = _veltkamp(b)
+    e = ((ah * bh - p) + ah * bl + al * bh) + al * bl
+    return p, e
+
+
+def residual_exact(A, b, x, rows=None):
+    """r_j = b_j - sum_k A_jk x_k rounded once to FP64 (the residual of the
+    Algorithm 2 loop in exact arithmetic): every product split exactly into
+    two doubles, then math.fsum (exact sum, one rounding).  rows: indices to
+    compute (default all).  For the error analysis of Sec. 4.3 this is r(x)
+    with f = 0 up to a final rounding."""
+    import math
+
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    rows = range(A.shape[0]) if rows is None else rows
+    out = []
+    for j in rows:
+        p, e = two_product(A[j], x)
+        out.append(math.fsum([float(b[j]), *(-p).tolist(), *(-e).tolist()]))
+    return np.array(out)
+
+
+def gradient_exact(A, r, cols=None):
+    """c_k = sum_j A_jk r_j rounded once to FP64 (A^T r in exact arithmetic,
+    same construction as residual_exact)."""
+    import math
+
+    A = np.asarray(A, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    cols = range(A.shape[1]) if cols is None else cols
+    out = []
+    for k in cols:
+        p, e = two_product(A[:, k], r)
+        out.append(math.fsum([*p.tolist(), *e.tolist()]))
+    return np.array(out)
+
+
 def iterate(A, b, R, x0, q: int, normest_value: float, condest_value: float, *,
             use_stop: bool = True, extra: int = 0, gamma: float = 1.0, rho: float = 0.04,
             variant: int = 0, alpha: float = 1.0, beta: float = 0.0):

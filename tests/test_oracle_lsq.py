@@ -88,6 +88,30 @@ def test_residual_gradient_rounding_bound():
     assert np.abs(c - cl).max() < 1e-8 * np.abs(c).max()
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_exact_residual_and_gradient_vs_rationals(seed):
+    """residual_exact / gradient_exact are the correctly rounded r = b - A x
+    and c = A^T r: checked against exact rational sums (entries spread over
+    many binades, cancellation in b - A x)."""
+    rng = np.random.default_rng(seed)
+    m, n = 23, 9
+    A = rng.standard_normal((m, n)) * np.exp(rng.uniform(-20, 20, (m, n)))
+    x = rng.standard_normal(n) * np.exp(rng.uniform(-10, 10, n))
+    b = A @ x * (1 + 1e-12 * rng.standard_normal(m))
+    r = oracle.residual_exact(A, b, x)
+    for j in range(m):
+        ex = Fr(float(b[j])) - sum(Fr(float(A[j, k])) * Fr(float(x[k])) for k in range(n))
+        assert r[j] == float(ex), j                  # float(Fraction) rounds to nearest
+    c = oracle.gradient_exact(A, r)
+    for k in range(n):
+        ex = sum(Fr(float(A[j, k])) * Fr(float(r[j])) for j in range(m))
+        assert c[k] == float(ex), k
+    # and the plain FP64 pass is within its rounding bound of them
+    ro, co = oracle.residual_gradient(A, b, x)
+    g = (n + 1) * U / (1 - (n + 1) * U)
+    assert np.all(np.abs(ro - r) <= 2 * g * (np.abs(b) + np.abs(A) @ np.abs(x)))
+
+
 def test_substitutions_backward_stable():
     rng = np.random.default_rng(2)
     n = 60
@@ -123,6 +147,84 @@ def test_one_refinement_step_vs_exact_rationals():
     want = np.array([float(Fr(float(x0[k])) + dlt[k]) for k in range(n)])
     kR = np.linalg.cond(R)
     assert np.linalg.norm(x1 - want) <= 50 * n * m * U * kR ** 2 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("alpha,beta", [(0.75, 0.0), (0.9, 0.05), (1.0, 0.3)])
+def test_two_damped_momentum_steps_vs_exact_rationals(alpha, beta):
+    """App. B, Eq. (B.1): x_{i+1} = x_i + alpha d_i + beta (x_i - x_{i-1}) with
+    d_i = R^{-1} R^{-T} A^T (b - A x_i) and x_{-1} = x_0 (the first step has no
+    momentum).  Two steps against the same recurrence over the rationals."""
+    rng = np.random.default_rng(9)
+    m, n = 12, 3
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m)
+    R = np.linalg.qr(A + 0.05 * rng.standard_normal((m, n)), mode="r")
+    x0 = rng.standard_normal(n)
+    x2, info = oracle.iterate(A, b, R, x0, q=2, normest_value=1.0, condest_value=1.0, use_stop=False,
+                              alpha=alpha, beta=beta)
+    assert info["iters"] == 2
+    Af = [[Fr(float(A[i, j])) for j in range(n)] for i in range(m)]
+    Rf = [[Fr(float(R[i, j])) for j in range(n)] for i in range(n)]
+    RtR = [[sum(Rf[k][i] * Rf[k][j] for k in range(n)) for j in range(n)] for i in range(n)]
+    a, bt = Fr(alpha), Fr(beta)
+    xp = [Fr(float(v)) for v in x0]
+    xc = list(xp)
+    for _ in range(2):
+        rr = [Fr(float(b[i])) - sum(Af[i][k] * xc[k] for k in range(n)) for i in range(m)]
+        c = [sum(Af[i][k] * rr[i] for i in range(m)) for k in range(n)]
+        dl = exact_solve(RtR, c)
+        xn = [xc[k] + a * dl[k] + bt * (xc[k] - xp[k]) for k in range(n)]
+        xp, xc = xc, xn
+    want = np.array([float(v) for v in xc])
+    kR = np.linalg.cond(R)
+    assert np.linalg.norm(x2 - want) <= 100 * n * m * U * kR ** 2 * np.linalg.norm(want)
+    # the momentum term is really there: beta = 0 gives a different second step
+    if beta:
+        x2b, _ = oracle.iterate(A, b, R, x0, q=2, normest_value=1.0, condest_value=1.0, use_stop=False,
+                                alpha=alpha, beta=0.0)
+        assert np.linalg.norm(x2b - want) > 1e3 * np.linalg.norm(x2 - want) + 1e-14
+
+
+def halving_problem(m=8, n=2):
+    """A = [I_n; 0], b = e_1, R = I: with alpha = 1/2 the iterates from x_0 = 0
+    are x_i = (1 - 2^-i) e_1 and r(x_i) = 2^-i e_1 EXACTLY in FP64, so
+    ||r(x_i) - r(x_{i-1})|| = 2^-i and ||r(x_i)|| = 2^-i."""
+    A = np.zeros((m, n))
+    A[:n, :n] = np.eye(n)
+    b = np.zeros(m)
+    b[0] = 1.0
+    return A, b, np.eye(n)
+
+
+@pytest.mark.parametrize("extra", [0, 1, 3])
+def test_stopping_rule_normest_term_fires_at_the_predicted_step(extra):
+    """Sec. 3.3 rule ||r(x_{i+1}) - r(x_i)|| <= u (gamma normest ||x_{i+1}|| +
+    rho condest ||r(x_{i+1})||) with gamma = 1, normest = 2^10, rho = 0: on the
+    halving problem it first holds at i = 44 (2^-44 <= 2^-43 (1 - 2^-44), while
+    2^-43 > 2^-43 (1 - 2^-43)), and x_44 is returned after `extra` more
+    updates."""
+    A, b, R = halving_problem()
+    x, info = oracle.iterate(A, b, R, np.zeros(2), 100, 1024.0, 1.0, use_stop=True, extra=extra,
+                             gamma=1.0, rho=0.0, alpha=0.5)
+    assert info["converged"] and info["iters"] == 44 + extra
+    assert x[0] == 1.0 - 2.0 ** -(44 + extra) and x[1] == 0.0
+    # the rule compares the change of residual (2^-i), not the residual of x_0
+    assert info["step_norm"] == 2.0 ** -(44 + extra)
+
+
+def test_stopping_rule_condest_term_uses_the_new_residual():
+    """gamma = 0: the rule reads 2^-i <= u rho condest 2^-i, i.e. it holds at
+    the first test (i = 1) exactly when rho condest >= 2^53 and never when it
+    is below: the condest term is rho condest ||r(x_{i+1})|| with the current
+    residual."""
+    A, b, R = halving_problem()
+    rho = 0.04
+    ce_hi = 2.0 ** 53 / rho * (1 + 1e-9)
+    ce_lo = 2.0 ** 53 / rho * (1 - 1e-9)
+    x, info = oracle.iterate(A, b, R, np.zeros(2), 30, 1.0, ce_hi, use_stop=True, gamma=0.0, rho=rho, alpha=0.5)
+    assert info["converged"] and info["iters"] == 1 and x[0] == 0.5
+    x, info = oracle.iterate(A, b, R, np.zeros(2), 30, 1.0, ce_lo, use_stop=True, gamma=0.0, rho=rho, alpha=0.5)
+    assert not info["converged"] and info["iters"] == 30
 
 
 def _setup(P, d=1000, zeta=8, seed=0):
