@@ -144,13 +144,59 @@ LS_API ls_status ls_residual_gradient(ls_ctx* ctx, const double* A, int64_t m, i
                                const double* b, const double* x, const double* r_prev,
                                double* r_out, double* c, double* norms);
 
+/* (a6 as ls_iterate runs it for n <= 1024) A in fixed point, so that the
+ * fused pass runs on the integer multiply-add units (no counterpart in the
+ * paper's pseudocode: it is how this library forms the Algorithm 2 residual
+ * and gradient to the accuracy Sec. 4.3, Eqs. (4.8)-(4.9), asks of them).
+ * Row j is written as A_fx[2 (j ldf + k)] = lo, A_fx[2 (j ldf + k) + 1] = hi
+ * with A[j, k] ~= (hi 2^28 + lo) 2^(row_exp[j] - 1077), 0 <= lo < 2^28, where
+ * row_exp[j] is the largest biased FP64 exponent field in the row (at least
+ * 1): entries within two binades of the row's largest are exact, smaller ones
+ * are rounded to nearest, an error below 2^-55 of the row's largest
+ * magnitude.  A_fx: m x ldf pairs of int32 (device, 16-byte aligned, ldf even,
+ * ldf >= n); row_exp: m int32 (device).  A as for ls_residual_gradient.
+ * LS_ENONFINITE if A holds an Inf or NaN (those rows are written as zero). */
+LS_API ls_status ls_fixed_point(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda,
+                                int32_t* A_fx, int64_t ldf, int32_t* row_exp);
+
+/* (a6) The fused residual/gradient pass of ls_residual_gradient on the fixed-
+ * point A of ls_fixed_point (n <= 1024): r = b - A x and c = A^T r.  The row
+ * dots and the column sums are exact integer sums of the 55-bit fixed-point
+ * products (x is put in fixed point with one exponent; r_j with one exponent
+ * per CTA), each result rounded once to FP64, so r and c differ from the
+ * exact values for the fixed-point A by about one rounding.  Bit-identical run
+ * to run.  Outputs and r_prev / r_out rules as ls_residual_gradient; a
+ * non-finite x or r makes c and norms NaN. */
+LS_API ls_status ls_residual_gradient_fx(ls_ctx* ctx, const int32_t* A_fx, const int32_t* row_exp, int64_t m,
+                                         int64_t n, int64_t ldf, const double* b, const double* x,
+                                         const double* r_prev, double* r_out, double* c, double* norms);
+
+/* Bounded device waits of the fixed-point pass give up after `ns`
+ * nanoseconds (0: the default, 2 s), set LS_ETIMEOUT and let the kernel
+ * return; the context stays usable.  No counterpart in the paper. */
+LS_API ls_status ls_set_wait_limit(ls_ctx* ctx, uint64_t ns);
+
+/* Failure injection for tests (no counterpart in the paper).  The fault is
+ * made on the host side of the library and consumed by the next call it
+ * applies to:
+ *   LS_FAULT_SKIP_TILE: in the next fixed-point pass, CTA 0's producer does
+ *     not issue its tile number `arg`, so the consumers' bounded waits run
+ *     out (with the wait limit above) and the call returns LS_ETIMEOUT;
+ *   LS_FAULT_ALLOC: the next device scratch allocation fails (LS_ENOMEM);
+ *   LS_FAULT_NONE: clear both. */
+enum { LS_FAULT_NONE = 0, LS_FAULT_SKIP_TILE = 1, LS_FAULT_ALLOC = 2 };
+LS_API ls_status ls_inject_fault(ls_ctx* ctx, int kind, int64_t arg);
+
 /* (a7) The correction of Algorithm 2: y = R^{-T} c, d = R^{-1} y (two
  * triangular solves), x <- x + d.  y_out, d_out (n doubles) may be NULL. */
 LS_API ls_status ls_correct(ls_ctx* ctx, const double* R, int64_t ldr, int64_t n, const double* c,
                      double* x, double* y_out, double* d_out);
 
 /* (a6-a7) Iterate from x (in: start, out: final iterate), at most q updates,
- * with the Sec. 3.3 stopping rule (opts may be NULL for defaults).
+ * with the Sec. 3.3 stopping rule (opts may be NULL for defaults).  For
+ * n <= 1024 each call first puts A in fixed point (ls_fixed_point, in the
+ * context's scratch: 8 m (n rounded up to even) + 4 m bytes) and runs the
+ * fixed-point pass; above that the FP64 pass of ls_residual_gradient.
  * normest/condest come from ls_factor (pass info from ls_factor, or set
  * info->normest/condest); info must not be NULL.  Resumable: calling twice
  * with q1 then q2 and use_stop = 0 equals one call with q1 + q2.
@@ -159,6 +205,23 @@ LS_API ls_status ls_correct(ls_ctx* ctx, const double* R, int64_t ldr, int64_t n
 LS_API ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda,
                      const double* b, const double* R, int64_t ldr, double* x, int q,
                      const ls_opts* opts, ls_info* info);
+
+/* (a6-a7, row-sharded) ls_iterate with the rows of A and b split into
+ * `nparts` parts: part p is A_parts[p] (m_parts[p] x n, row-major, leading
+ * dimension lda, device) and b_parts[p] (m_parts[p]).  This is the
+ * data-parallel form of the Algorithm 2 loop: every part forms its own
+ * partial A^T r, ||r||^2 and ||r - r_prev||^2 (the fixed-point pass), the
+ * partials are reduced in part order (exact integer sums of the column
+ * partials, FP64 norm sums in part order), and R, x and the two substitutions
+ * are shared.  On several GPUs each part would live on its own device with
+ * one exchange of the partials per iteration; here all parts run on the
+ * context's device.  n <= 1024, 1 <= nparts <= 64.  Results are bit-identical
+ * run to run for a given split (the fixed-point exponents are per CTA, so a
+ * different split rounds r differently, within the same bounds).  Other
+ * arguments and status as ls_iterate. */
+LS_API ls_status ls_iterate_rows(ls_ctx* ctx, int nparts, const double* const* A_parts, const int64_t* m_parts,
+                                 int64_t n, int64_t lda, const double* const* b_parts, const double* R, int64_t ldr,
+                                 double* x, int q, const ls_opts* opts, ls_info* info);
 
 /* One problem of a batch (ls_solve_batched).  All pointers are device
  * pointers: row-major A (m x n, lda even >= n, 16-byte aligned), b (m), x (n,
@@ -314,8 +377,11 @@ LS_API ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int6
  * so those callers use this entry point instead; it needs no context.
  *
  * Computes exactly what ls_residual_gradient computes (same kernels, same
- * fixed summation order, so the same bits), on `cuda_stream` (a cudaStream_t,
- * 0 = the legacy default stream) of the CURRENT device.  The caller still
+ * fixed summation order, so the same bits on a device with at most 160 SMs,
+ * such as GB300's 152; a larger device runs the pass on 160 CTAs, which
+ * changes the order of the per-CTA sums but not their bounds), on
+ * `cuda_stream` (a cudaStream_t, 0 = the legacy default stream) of the
+ * CURRENT device.  The caller still
  * passes every input and output (device memory).  The per-CTA partial sums
  * live in a fixed array inside the library, about 1.3 MB, which every GPU
  * that loads the library holds until the process exits.

@@ -17,6 +17,7 @@ import os
 from .build import LIB as _LIB_PATH
 
 LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ERANK, LS_ENONFINITE, LS_ETIMEOUT, LS_ENOTCONV = range(8)
+LS_FAULT_NONE, LS_FAULT_SKIP_TILE, LS_FAULT_ALLOC = range(3)
 STATUS_NAMES = ["LS_OK", "LS_EINVAL", "LS_ENOMEM", "LS_ECUDA", "LS_ERANK", "LS_ENONFINITE", "LS_ETIMEOUT",
                 "LS_ENOTCONV"]
 
@@ -125,6 +126,17 @@ def lib():
     L.ls_server_get_stats.restype = S
     L.ls_residual_gradient_noalloc.argtypes = [P, P, I64, I64, I64, P, P, P, P, P, P]
     L.ls_residual_gradient_noalloc.restype = S
+    L.ls_fixed_point.argtypes = [P, P, I64, I64, I64, P, I64, P]
+    L.ls_fixed_point.restype = S
+    L.ls_residual_gradient_fx.argtypes = [P, P, P, I64, I64, I64, P, P, P, P, P, P]
+    L.ls_residual_gradient_fx.restype = S
+    L.ls_set_wait_limit.argtypes = [P, C.c_uint64]
+    L.ls_set_wait_limit.restype = S
+    L.ls_iterate_rows.argtypes = [P, I, C.POINTER(P), C.POINTER(I64), I64, I64, C.POINTER(P), P, I64, P, I,
+                                  C.POINTER(ls_opts), C.POINTER(ls_info)]
+    L.ls_iterate_rows.restype = S
+    L.ls_inject_fault.argtypes = [P, I, I64]
+    L.ls_inject_fault.restype = S
     _lib = L
     return L
 
@@ -223,6 +235,30 @@ class Context:
     def ls_residual_gradient(self, A, m, n, lda, b, x, r_prev, r_out, c, norms):
         return self._check(lib().ls_residual_gradient(self._h, _ptr(A), m, n, lda, _ptr(b), _ptr(x),
                                                       _ptr(r_prev), _ptr(r_out), _ptr(c), _ptr(norms)))
+
+    def ls_fixed_point(self, A, m, n, lda, A_fx, ldf, row_exp):
+        return self._check(lib().ls_fixed_point(self._h, _ptr(A), m, n, lda, _ptr(A_fx), ldf, _ptr(row_exp)))
+
+    def ls_residual_gradient_fx(self, A_fx, row_exp, m, n, ldf, b, x, r_prev, r_out, c, norms):
+        return self._check(lib().ls_residual_gradient_fx(self._h, _ptr(A_fx), _ptr(row_exp), m, n, ldf, _ptr(b),
+                                                         _ptr(x), _ptr(r_prev), _ptr(r_out), _ptr(c), _ptr(norms)))
+
+    def ls_iterate_rows(self, A_parts, m_parts, n, lda, b_parts, R, ldr, x, q, opts=None, info=None):
+        info = info if info is not None else ls_info()
+        k = len(A_parts)
+        Ap = (C.c_void_p * k)(*[_ptr(a) for a in A_parts])
+        bp = (C.c_void_p * k)(*[_ptr(b) for b in b_parts])
+        mp = (C.c_int64 * k)(*m_parts)
+        st = lib().ls_iterate_rows(self._h, k, Ap, mp, n, lda, bp, _ptr(R), ldr, _ptr(x), q,
+                                   C.byref(opts) if opts is not None else None, C.byref(info))
+        self._check(st, allow=(LS_OK, LS_ENOTCONV))
+        return st, info
+
+    def ls_set_wait_limit(self, ns):
+        return self._check(lib().ls_set_wait_limit(self._h, ns))
+
+    def ls_inject_fault(self, kind, arg=0):
+        return self._check(lib().ls_inject_fault(self._h, kind, arg))
 
     def ls_correct(self, R, ldr, n, c, x, y_out=None, d_out=None):
         return self._check(lib().ls_correct(self._h, _ptr(R), ldr, n, _ptr(c), _ptr(x), _ptr(y_out), _ptr(d_out)))

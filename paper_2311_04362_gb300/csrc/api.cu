@@ -52,6 +52,10 @@ struct Carve {
 
 ls_status ensure_arena(ls_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->arena_bytes) return LS_OK;
+  if (ctx->inject_alloc_fail) {                 // test hook (ls_inject_fault)
+    ctx->inject_alloc_fail = 0;
+    return fail(ctx, LS_ENOMEM, "device scratch of %zu bytes could not be allocated (injected failure)", bytes);
+  }
   if (ctx->arena) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->arena);
@@ -196,6 +200,23 @@ IterScratch carve_iter(Carve& c, const PassGeom& g, int64_t m, int64_t n) {
   return s;
 }
 
+// Fixed-point pass (fxpass.cu): A in 55-bit fixed point, row exponents and
+// the per-CTA partials.  Used by the iteration for n <= kFxMaxN.
+bool use_fx_pass(int64_t n) { return n <= kFxMaxN; }
+
+struct FxScratch {
+  int2* Af; int* rexp; long long* part; int64_t ldf;
+};
+FxScratch carve_fx(Carve& c, const ls_ctx* ctx, int64_t m, int64_t n) {
+  FxScratch f;
+  f.ldf = (n + 1) & ~1LL;
+  const FxGeom g = fx_geometry(ctx, n, m);
+  f.Af = c.take<int2>((size_t)m * f.ldf);
+  f.rexp = c.take<int>((size_t)m);
+  f.part = c.take<long long>(fx_part_words(g, n));
+  return f;
+}
+
 }  // namespace
 
 // ============================================================ public API
@@ -304,6 +325,7 @@ size_t ls_workspace_bytes(int64_t m, int64_t n, int64_t d, int zeta) {
   c.off = mark;
   PassGeom g = pass_geometry(&probe, n, m);
   carve_iter(c, g, m, n);
+  if (use_fx_pass(n)) carve_fx(c, &probe, m, n);
   size_t it = c.off;
   size_t need = std::max(sk, std::max(fa, it));
   return need;
@@ -478,6 +500,69 @@ ls_status ls_residual_gradient(ls_ctx* ctx, const double* A, int64_t m, int64_t 
   return sync_and_check(ctx);
 }
 
+ls_status ls_fixed_point(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, int32_t* A_fx,
+                         int64_t ldf, int32_t* row_exp) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st;
+  if (m < 1 || m > INT32_MAX) return fail(ctx, LS_EINVAL, "m = %lld out of range [1, 2^31-1]", (long long)m);
+  if ((st = check_A(ctx, A, m, n, lda))) return st;
+  if (!A_fx || !row_exp) return fail(ctx, LS_EINVAL, "null pointer argument");
+  if (ldf < n || (ldf & 1)) return fail(ctx, LS_EINVAL, "ldf = %lld must be even and >= n", (long long)ldf);
+  if (reinterpret_cast<uintptr_t>(A_fx) & 15) return fail(ctx, LS_EINVAL, "A_fx must be 16-byte aligned");
+  cudaSetDevice(ctx->device);
+  if ((st = reset_status(ctx))) return st;
+  CUDA_TRY(ctx, launch_to_fixed(ctx, A, m, n, lda, reinterpret_cast<int2*>(A_fx), ldf, row_exp));
+  return sync_and_check(ctx);
+}
+
+ls_status ls_residual_gradient_fx(ls_ctx* ctx, const int32_t* A_fx, const int32_t* row_exp, int64_t m, int64_t n,
+                                  int64_t ldf, const double* b, const double* x, const double* r_prev, double* r_out,
+                                  double* c, double* norms) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st;
+  if (m < 1 || m > INT32_MAX) return fail(ctx, LS_EINVAL, "m = %lld out of range [1, 2^31-1]", (long long)m);
+  if (n < 1 || n > m) return fail(ctx, LS_EINVAL, "need 1 <= n <= m (n = %lld, m = %lld)", (long long)n, (long long)m);
+  if (n > kFxMaxN) return fail(ctx, LS_EINVAL, "n = %lld above the fixed-point pass limit %lld", (long long)n,
+                               (long long)kFxMaxN);
+  if (!A_fx || !row_exp || !b || !x || !c || !norms) return fail(ctx, LS_EINVAL, "null pointer argument");
+  if (ldf < n || (ldf & 1)) return fail(ctx, LS_EINVAL, "ldf = %lld must be even and >= n", (long long)ldf);
+  if (reinterpret_cast<uintptr_t>(A_fx) & 15) return fail(ctx, LS_EINVAL, "A_fx must be 16-byte aligned");
+  cudaSetDevice(ctx->device);
+  const FxGeom g = fx_geometry(ctx, n, m);
+  Carve probe(nullptr);
+  probe.take<long long>(fx_part_words(g, n));
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  long long* part = cc.take<long long>(fx_part_words(g, n));
+  CUtensorMap map;
+  CUDA_TRY(ctx, make_fx_tensor_map(ctx, &map, reinterpret_cast<const int2*>(A_fx), m, n, ldf, g));
+  if ((st = reset_status(ctx))) return st;
+  CUDA_TRY(ctx, launch_fx_pass(ctx, map, g, m, n, row_exp, b, x, r_prev, r_out, part, nullptr));
+  CUDA_TRY(ctx, launch_fx_reduce(ctx, part, g.grid, n, c, norms, nullptr));
+  if (!r_prev) CUDA_TRY(ctx, cudaMemsetAsync(norms + 1, 0, sizeof(double), ctx->stream));
+  return sync_and_check(ctx);
+}
+
+ls_status ls_set_wait_limit(ls_ctx* ctx, uint64_t ns) {
+  if (!ctx) return LS_EINVAL;
+  ctx->wait_ns = ns ? ns : LS_WAIT_NS;
+  return LS_OK;
+}
+
+ls_status ls_inject_fault(ls_ctx* ctx, int kind, int64_t arg) {
+  if (!ctx) return LS_EINVAL;
+  if (kind == LS_FAULT_NONE) { ctx->inject_skip_tile = -1; ctx->inject_alloc_fail = 0; return LS_OK; }
+  if (kind == LS_FAULT_SKIP_TILE) {
+    if (arg < 0 || arg > INT32_MAX) return fail(ctx, LS_EINVAL, "tile index out of range");
+    ctx->inject_skip_tile = (int)arg;
+    return LS_OK;
+  }
+  if (kind == LS_FAULT_ALLOC) { ctx->inject_alloc_fail = 1; return LS_OK; }
+  return fail(ctx, LS_EINVAL, "unknown fault kind %d", kind);
+}
+
 ls_status ls_correct(ls_ctx* ctx, const double* R, int64_t ldr, int64_t n, const double* c, double* x, double* y_out,
                      double* d_out) {
   if (!ctx) return LS_EINVAL;
@@ -515,8 +600,19 @@ static ls_status iterate_impl(ls_ctx* ctx, const double* A, int64_t m, int64_t n
   if (opts) o = *opts;
   PassGeom g = pass_geometry(ctx, n, m);
   IterScratch s = carve_iter(cc, g, m, n);
+  const bool fx = use_fx_pass(n);
   CUtensorMap map;
-  CUDA_TRY(ctx, make_tensor_map(ctx, &map, A, m, n, lda, g));
+  FxScratch fs{};
+  FxGeom fg{};
+  if (fx) {
+    // A in fixed point once per call; every pass then reads the 8-byte limbs
+    fs = carve_fx(cc, ctx, m, n);
+    fg = fx_geometry(ctx, n, m);
+    CUDA_TRY(ctx, launch_to_fixed(ctx, A, m, n, lda, fs.Af, fs.ldf, fs.rexp));
+    CUDA_TRY(ctx, make_fx_tensor_map(ctx, &map, fs.Af, m, n, fs.ldf, fg));
+  } else {
+    CUDA_TRY(ctx, make_tensor_map(ctx, &map, A, m, n, lda, g));
+  }
   CUDA_TRY(ctx, launch_prepare_R(ctx, R, ldr, n, nullptr, n, s.Rt, s.inv_diag));
   IterState h{};
   h.gamma = o.gamma; h.rho = o.rho; h.alpha = o.alpha; h.beta = o.beta;
@@ -527,7 +623,7 @@ static ls_status iterate_impl(ls_ctx* ctx, const double* A, int64_t m, int64_t n
   CUDA_TRY(ctx, cudaMemcpyAsync(s.x_prev, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   CUDA_TRY(ctx, cudaMemsetAsync(s.r_prev, 0, sizeof(double) * m, ctx->stream));
   StepArgs a{};
-  a.part = s.part; a.nparts = g.grid; a.Rt = s.Rt; a.R = R; a.ldr = ldr; a.inv_diag = s.inv_diag; a.n = (int)n;
+  a.part = s.part; a.nparts = fx ? 1 : g.grid; a.Rt = s.Rt; a.R = R; a.ldr = ldr; a.inv_diag = s.inv_diag; a.n = (int)n;
   a.x = x; a.x_prev = s.x_prev; a.y = s.y; a.dvec = s.dvec; a.work = s.work; a.slots = s.slots; a.st = s.st;
   a.use_stop = o.use_stop; a.extra = o.extra_iters; a.status = ctx->d_status;
   // launch in chunks; between chunks read the done flag.  Each fused pass is
@@ -544,8 +640,14 @@ static ls_status iterate_impl(ls_ctx* ctx, const double* A, int64_t m, int64_t n
     const int k = std::min(chunk, q - launched);
     for (int i = 0; i < k; ++i) {
       CUDA_TRY(ctx, cudaEventRecord(ctx->pass_ev[2 * (launched + i)], ctx->stream));
-      CUDA_TRY(ctx, launch_fused_pass(ctx, map, g, m, n, b, x, s.r_prev, s.r_prev, s.part, s.st));
-      CUDA_TRY(ctx, cudaEventRecord(ctx->pass_ev[2 * (launched + i) + 1], ctx->stream));
+      if (fx) {
+        CUDA_TRY(ctx, launch_fx_pass(ctx, map, fg, m, n, fs.rexp, b, x, s.r_prev, s.r_prev, fs.part, s.st));
+        CUDA_TRY(ctx, cudaEventRecord(ctx->pass_ev[2 * (launched + i) + 1], ctx->stream));
+        CUDA_TRY(ctx, launch_fx_reduce(ctx, fs.part, fg.grid, n, s.part, s.part + n, s.st));
+      } else {
+        CUDA_TRY(ctx, launch_fused_pass(ctx, map, g, m, n, b, x, s.r_prev, s.r_prev, s.part, s.st));
+        CUDA_TRY(ctx, cudaEventRecord(ctx->pass_ev[2 * (launched + i) + 1], ctx->stream));
+      }
       CUDA_TRY(ctx, launch_iter_step(ctx, a));
     }
     launched += k;
@@ -581,6 +683,129 @@ static ls_status iterate_impl(ls_ctx* ctx, const double* A, int64_t m, int64_t n
   return LS_OK;
 }
 
+// Row-sharded iteration on one device: part p holds rows m_parts[p] of A and
+// b.  Each iteration runs the fixed-point pass on every part into its own
+// block of per-CTA partials (what one GPU of a row-sharded run computes),
+// then one reduction over all blocks in part order (the exchange: exact
+// integer sums of the column partials, FP64 norms in order), then the step.
+static ls_status iterate_rows_impl(ls_ctx* ctx, int np, const double* const* A_parts, const int64_t* m_parts,
+                                   int64_t n, int64_t lda, const double* const* b_parts, const double* R, int64_t ldr,
+                                   double* x, int q, const ls_opts* opts, double normest, double condest, Carve& cc,
+                                   ls_info* info) {
+  ls_opts o;
+  ls_default_opts(&o);
+  if (opts) o = *opts;
+  int64_t mtot = 0;
+  for (int p = 0; p < np; ++p) mtot += m_parts[p];
+  PassGeom g0 = pass_geometry(ctx, n, mtot);
+  IterScratch s = carve_iter(cc, g0, mtot, n);        // step scratch; r_prev for all rows
+  std::vector<FxScratch> fs(np);
+  std::vector<FxGeom> fg(np);
+  std::vector<CUtensorMap> maps(np);
+  std::vector<int64_t> roff(np), poff(np);
+  int64_t rsum = 0, psum = 0;
+  for (int p = 0; p < np; ++p) {
+    fg[p] = fx_geometry(ctx, n, m_parts[p]);
+    fs[p] = carve_fx(cc, ctx, m_parts[p], n);
+    roff[p] = rsum;
+    poff[p] = psum;
+    rsum += m_parts[p];
+    psum += (int64_t)fx_part_words(fg[p], n);
+  }
+  long long* allpart = cc.take<long long>((size_t)psum);
+  int ctas = 0;
+  for (int p = 0; p < np; ++p) {
+    CUDA_TRY(ctx, launch_to_fixed(ctx, A_parts[p], m_parts[p], n, lda, fs[p].Af, fs[p].ldf, fs[p].rexp));
+    CUDA_TRY(ctx, make_fx_tensor_map(ctx, &maps[p], fs[p].Af, m_parts[p], n, fs[p].ldf, fg[p]));
+    ctas += fg[p].grid;
+  }
+  CUDA_TRY(ctx, launch_prepare_R(ctx, R, ldr, n, nullptr, n, s.Rt, s.inv_diag));
+  IterState h{};
+  h.gamma = o.gamma; h.rho = o.rho; h.alpha = o.alpha; h.beta = o.beta;
+  h.normest = normest; h.condest = condest;
+  IterState* hs = reinterpret_cast<IterState*>(reinterpret_cast<char*>(ctx->h_pinned) + 256);
+  *hs = h;
+  CUDA_TRY(ctx, cudaMemcpyAsync(s.st, hs, sizeof(IterState), cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(s.x_prev, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemsetAsync(s.r_prev, 0, sizeof(double) * mtot, ctx->stream));
+  StepArgs a{};
+  a.part = s.part; a.nparts = 1; a.Rt = s.Rt; a.R = R; a.ldr = ldr; a.inv_diag = s.inv_diag; a.n = (int)n;
+  a.x = x; a.x_prev = s.x_prev; a.y = s.y; a.dvec = s.dvec; a.work = s.work; a.slots = s.slots; a.st = s.st;
+  a.use_stop = o.use_stop; a.extra = o.extra_iters; a.status = ctx->d_status;
+  const int chunk = 8;
+  int launched = 0;
+  IterState* hread = reinterpret_cast<IterState*>(reinterpret_cast<char*>(ctx->h_pinned) + 1024);
+  while (launched < q) {
+    const int k = std::min(chunk, q - launched);
+    for (int i = 0; i < k; ++i) {
+      for (int p = 0; p < np; ++p)
+        CUDA_TRY(ctx, launch_fx_pass(ctx, maps[p], fg[p], m_parts[p], n, fs[p].rexp, b_parts[p], x,
+                                     s.r_prev + roff[p], s.r_prev + roff[p], allpart + poff[p], s.st));
+      CUDA_TRY(ctx, launch_fx_reduce(ctx, allpart, ctas, n, s.part, s.part + n, s.st));
+      CUDA_TRY(ctx, launch_iter_step(ctx, a));
+    }
+    launched += k;
+    if (launched < q) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(hread, s.st, sizeof(IterState), cudaMemcpyDeviceToHost, ctx->stream));
+      CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      if (hread->done) break;
+    }
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(hread, s.st, sizeof(IterState), cudaMemcpyDeviceToHost, ctx->stream));
+  ls_status st = sync_and_check(ctx);
+  if (st) return st;
+  if (info) {
+    info->iters = hread->iter;
+    info->res_norm = hread->rnorm;
+    info->step_norm = hread->dnorm;
+    info->normest = normest;
+    info->condest = condest;
+    info->stop_reason = hread->done ? (hread->nonfinite ? 3 : 0) : (o.use_stop ? 1 : 2);
+  }
+  if (hread->nonfinite) return fail(ctx, LS_ENONFINITE, "the iterate became non-finite");
+  if (!hread->done && o.use_stop) return LS_ENOTCONV;
+  return LS_OK;
+}
+
+ls_status ls_iterate_rows(ls_ctx* ctx, int nparts, const double* const* A_parts, const int64_t* m_parts, int64_t n,
+                          int64_t lda, const double* const* b_parts, const double* R, int64_t ldr, double* x, int q,
+                          const ls_opts* opts, ls_info* info) {
+  if (!ctx) return LS_EINVAL;
+  ctx->err.clear();
+  ls_status st;
+  if (nparts < 1 || nparts > 64 || !A_parts || !m_parts || !b_parts)
+    return fail(ctx, LS_EINVAL, "need 1 <= nparts <= 64 and the part arrays");
+  if (n < 1 || n > kFxMaxN) return fail(ctx, LS_EINVAL, "need 1 <= n <= %lld", (long long)kFxMaxN);
+  int64_t mtot = 0;
+  for (int p = 0; p < nparts; ++p) {
+    if (m_parts[p] < 1 || m_parts[p] > INT32_MAX) return fail(ctx, LS_EINVAL, "part %d: m out of range", p);
+    if (!A_parts[p] || !b_parts[p]) return fail(ctx, LS_EINVAL, "part %d: null pointer", p);
+    if (lda < n || (lda & 1)) return fail(ctx, LS_EINVAL, "lda = %lld must be even and >= n", (long long)lda);
+    mtot += m_parts[p];
+  }
+  if (n > mtot) return fail(ctx, LS_EINVAL, "need n <= total rows");
+  if (!R || !x || !info) return fail(ctx, LS_EINVAL, "null pointer argument (info is required)");
+  if (ldr < n) return fail(ctx, LS_EINVAL, "ldr < n");
+  if (q < 0) return fail(ctx, LS_EINVAL, "q < 0");
+  cudaSetDevice(ctx->device);
+  Carve probe(nullptr);
+  carve_iter(probe, pass_geometry(ctx, n, mtot), mtot, n);
+  int64_t psum = 0;
+  for (int p = 0; p < nparts; ++p) {
+    carve_fx(probe, ctx, m_parts[p], n);
+    psum += (int64_t)fx_part_words(fx_geometry(ctx, n, m_parts[p]), n);
+  }
+  probe.take<long long>((size_t)psum);
+  if ((st = ensure_arena(ctx, probe.off))) return st;
+  Carve cc(ctx->arena);
+  if ((st = reset_status(ctx))) return st;
+  const double ne = info->normest, ce = info->condest;
+  const long long l0 = ctx->launches;
+  st = iterate_rows_impl(ctx, nparts, A_parts, m_parts, n, lda, b_parts, R, ldr, x, q, opts, ne, ce, cc, info);
+  info->launches = (int)(ctx->launches - l0);
+  return st;
+}
+
 ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                      const double* R, int64_t ldr, double* x, int q, const ls_opts* opts, ls_info* info) {
   if (!ctx) return LS_EINVAL;
@@ -596,6 +821,7 @@ ls_status ls_iterate(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
   PassGeom g = pass_geometry(ctx, n, m);
   Carve probe(nullptr);
   carve_iter(probe, g, m, n);
+  if (use_fx_pass(n)) carve_fx(probe, ctx, m, n);
   if ((st = ensure_arena(ctx, probe.off))) return st;
   Carve cc(ctx->arena);
   if ((st = reset_status(ctx))) return st;
@@ -1147,6 +1373,7 @@ ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int64_t m, 
   probe.off = mark;
   PassGeom g = pass_geometry(ctx, n, m);
   carve_iter(probe, g, m, n);
+  if (use_fx_pass(n)) carve_fx(probe, ctx, m, n);
   need = std::max(need, probe.off);
   if ((st = ensure_arena(ctx, need))) return st;
   Carve cc(ctx->arena);

@@ -1,0 +1,605 @@
+// fxpass.cu -- the fused residual/gradient pass of Algorithm 2 (a6) in exact
+// fixed-point integer arithmetic, so that it runs on the integer multiply-add
+// units instead of the FP64 pipe.
+//
+// Why: on GB300 an FP64 FMA issues at about 1.7 per SM clock while a 32x32 ->
+// 64-bit integer multiply-add (IMAD.WIDE) issues at about 60 (measured by
+// rates.cu).  The FP64 pass needs two FMAs per element of A and is bound by
+// that pipe at ~37% of HBM bandwidth.  Four IMAD.WIDE per element and
+// direction fit the integer units many times over, so this pass is bound by
+// the one read of A from HBM.
+//
+// Representation (exact, reversible up to the stated rounding):
+//  * A row j is held in 55-bit fixed point relative to its own binade bound:
+//    A_jk ~= a_jk 2^(e_j - 1077), |a_jk| < 2^55, where e_j is the largest
+//    biased FP64 exponent field of the row (subnormals count as 1).  Entries
+//    within 2 binades of the row's largest are exact; smaller ones are rounded
+//    to nearest (ties to even), an error below 2^-55 of the row's largest
+//    magnitude.  a = hi 2^28 + lo with 0 <= lo < 2^28, stored as int2 {lo, hi}.
+//  * x is held the same way with one exponent for the whole vector (per pass).
+//  * The row dot S_j = sum_k a_jk X_k is formed EXACTLY in 128-bit integers
+//    (hi*hi, hi*lo, lo*hi and lo*lo partial products, accumulated in 64-bit
+//    sums that cannot overflow for the bounded column counts per lane), so
+//    (A x)_j = S_j 2^(e_j + e_x - 2154) carries a single rounding when it is
+//    converted to FP64.  r_j = b_j - (A x)_j is formed in FP64.
+//  * For c = A^T r, rho_j = r_j 2^(e_j - 1077) is put in 55-bit fixed point
+//    with one exponent E per CTA (the largest seen so far; when a larger one
+//    arrives the CTA's accumulators are shifted right first), and
+//    sum_j a_jk P_j is accumulated exactly per column in 64-bit partial sums
+//    that are folded every <= 64 rows into a 128-bit accumulator in units of
+//    2^28 (the fold drops bits below 2^28 of a value of order 2^110).
+//  * The per-CTA accumulators are summed exactly by k_fx_reduce after
+//    alignment to the largest CTA exponent, and rounded once to FP64.
+// So r and c carry the rounding of A and x to 55 bits, one rounding each,
+// and no summation error: well inside the normwise bounds the analysis of
+// Sec. 4.3 (Eqs. (4.8)-(4.9)) asks of the residual and gradient, and tighter
+// than FP64 dot products (which err by ~sqrt(n) u).  Sums are exact, so the
+// results depend on the launch geometry only through the CTA exponents:
+// bit-identical run to run.
+//
+// k_fx_pass is warp-specialized (10 warps, one CTA per SM): a TMA producer
+// warp streams row tiles of the fixed-point A into a ring of shared stages;
+// warps 0-3 form the exact partial row dots of tile k (four independent
+// accumulator sets per lane, so that the integer multiply-add chains
+// overlap) and hand them over through a two-slot ring; one epilogue warp
+// finishes the rows (r_j, the norms, the fixed point of r_j) and hands them
+// to warps 4-7, which accumulate A^T r for their columns.  The three groups
+// work on different tiles at once; every hand-off is an mbarrier and every
+// wait is bounded by the context's wait limit (a group that gives up leaves
+// its loop as a whole warp, so no barrier is left waiting).
+#include "ls_internal.cuh"
+
+namespace lsk {
+
+namespace {
+
+constexpr int kFxRW = 4;                        // row-group warps
+constexpr int kFxCW = 4;                        // column-group warps
+constexpr int kFxThreads = (kFxRW + kFxCW + 2) * 32;   // + producer + epilogue warp
+constexpr int kFxFoldRows = 64;                 // column sums are folded at most every 64 rows
+constexpr int kNoExp = INT_MIN;                 // "no nonzero value yet"
+
+// |v| = M 2^(be - 1075), M < 2^53, be >= 1 (subnormals: be = 1, no implicit bit).
+__device__ __forceinline__ void fx_decode(uint64_t bits, uint64_t& M, int& be) {
+  const int e = (int)((bits >> 52) & 0x7FF);
+  M = bits & 0xFFFFFFFFFFFFFull;
+  if (e) M |= 1ull << 52;
+  be = e ? e : 1;
+}
+
+// round(M 2^s) for s <= 2, ties to even.
+__device__ __forceinline__ int64_t fx_round_shift(uint64_t M, int s) {
+  if (s >= 0) return (int64_t)(M << s);
+  const int r = -s;
+  if (r > 53) return 0;                          // M / 2^r < 1/2
+  const uint64_t q = M >> r;
+  const uint64_t rem = M & ((1ull << r) - 1);
+  const uint64_t half = 1ull << (r - 1);
+  return (int64_t)(q + ((rem > half) || (rem == half && (q & 1ull))));
+}
+
+// Fixed point of the FP64 `bits` relative to the binade bound `top`
+// (>= the value's be): v ~= F 2^(top - 1077), |F| < 2^55.
+__device__ __forceinline__ int64_t fx_of(uint64_t bits, int top) {
+  uint64_t M;
+  int be;
+  fx_decode(bits, M, be);
+  const int64_t F = fx_round_shift(M, be - top + 2);
+  return (bits >> 63) ? -F : F;
+}
+
+__device__ __forceinline__ int2 fx_limbs(int64_t F) {
+  return make_int2((int)(F & 0x0FFFFFFF), (int)(F >> 28));
+}
+
+__device__ __forceinline__ int64_t mad_wide(int a, int b, int64_t c) {
+  int64_t d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+// v 2^k for a finite double, exact unless the result leaves the normal range.
+__device__ __forceinline__ double scale2(double v, int k) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7FF);
+  if (v == 0.0) return v;
+  if (e != 0 && e + k >= 1 && e + k <= 2046)
+    return __longlong_as_double((long long)(bits + ((uint64_t)(int64_t)k << 52)));
+  return ldexp(v, k);
+}
+
+// Nearest FP64 to a 128-bit integer (two conversions and one FMA: within
+// 1.5 units in the last place).
+__device__ __forceinline__ double i128_to_double(__int128 s) {
+  const long long hi = (long long)(s >> 64);
+  const unsigned long long lo = (unsigned long long)s;
+  return fma((double)hi, 0x1p64, (double)lo);
+}
+
+__device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
+  const unsigned long long lo = (unsigned long long)v;
+  const long long hi = (long long)(v >> 64);
+  const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+  const long long hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+  return ((__int128)hi2 << 64) | (__int128)lo2;
+}
+
+__device__ __forceinline__ int warp_max_int(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- A -> fixed
+// One warp per row: the row's binade bound, then every entry in fixed point.
+__global__ void __launch_bounds__(256) k_to_fixed(const double* __restrict__ A, int64_t m, int n, int64_t lda,
+                                                  int2* __restrict__ Af, int64_t ldf, int* __restrict__ rexp,
+                                                  unsigned int* status) {
+  const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= m) return;
+  const unsigned long long* row = reinterpret_cast<const unsigned long long*>(A + j * lda);
+  int top = 1, bad = 0;
+  for (int k = lane; k < n; k += 32) {
+    const int e = (int)((__ldg(row + k) >> 52) & 0x7FF);
+    bad |= (e == 0x7FF);
+    top = max(top, e);
+  }
+  top = warp_max_int(top);
+  bad = __any_sync(0xffffffffu, bad);
+  if (bad && lane == 0) atomicOr(status, LS_DEV_NONFINITE);
+  int2* out = Af + j * ldf;
+  for (int k = lane; k < n; k += 32) out[k] = bad ? make_int2(0, 0) : fx_limbs(fx_of(__ldg(row + k), top));
+  if (lane == 0) rexp[j] = top;
+}
+
+// ----------------------------------------------------------------- the pass
+struct FxArgs {
+  int64_t m;
+  int n, boxw, nbox, tr, stages, ntiles;
+  const int* rexp;           // e_j per row
+  const double* b;
+  const double* x;
+  const double* r_prev;      // may be null
+  double* r_out;             // may be null (may equal r_prev)
+  long long* part;           // gridDim.x * (2 n + 4) words
+  const IterState* st;       // null: always run
+  unsigned int* status;
+  unsigned long long wait_ns;
+  int inject_skip;           // CTA 0's producer skips this tile (test hook; -1 none)
+};
+
+template <int NPT2>
+__global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant__ CUtensorMap map, FxArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (a.st && a.st->done) return;
+  const int n = a.n, tr = a.tr, boxw = a.boxw, nbox = a.nbox, S = a.stages;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  const size_t stage_elems = (size_t)tr * nbox * boxw;
+  const int pitch = (nbox == 1) ? boxw : 256;       // elements between rows of one box
+  // layout: tiles [S][stage] | p1 [2][kFxRW][tr] i128 | xs [n] | rslot [S][tr] | rshift [S] | barriers
+  int2* tiles = reinterpret_cast<int2*>(smem_raw);
+  __int128* p1 = reinterpret_cast<__int128*>(tiles + S * stage_elems);
+  int2* xs = reinterpret_cast<int2*>(p1 + 2 * kFxRW * tr);
+  int2* rslot = xs + ((n + 1) & ~1);
+  int* rshift = reinterpret_cast<int*>(rslot + S * tr);
+  uint64_t* full = reinterpret_cast<uint64_t*>(rshift + ((S + 1) & ~1));
+  uint64_t* empty = full + S;      // stage consumed (column group)
+  uint64_t* rready = empty + S;    // P of a tile written (epilogue warp)
+  uint64_t* rfree = rready + S;    // P of a tile consumed (column group)
+  uint64_t* pready = rfree + S;    // [2] row-dot partials of a tile written (row warps)
+  uint64_t* pfree = pready + 2;    // [2] row-dot partials read (epilogue warp)
+  __shared__ int s_xtop, s_xbad;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kFxCW);
+      mbar_init(&rready[s], 1);
+      mbar_init(&rfree[s], kFxCW);
+    }
+    for (int i = 0; i < 2; ++i) { mbar_init(&pready[i], kFxRW); mbar_init(&pfree[i], 1); }
+    fence_mbar_init();
+    s_xtop = 1;
+    s_xbad = 0;
+  }
+  __syncthreads();
+  // x in fixed point with one binade bound for the vector (the same in every CTA)
+  {
+    int top = 1, bad = 0;
+    const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(a.x);
+    for (int i = tid; i < n; i += blockDim.x) {
+      const int e = (int)((xb[i] >> 52) & 0x7FF);
+      bad |= (e == 0x7FF);
+      top = max(top, e);
+    }
+    top = warp_max_int(top);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) s_xbad = 1;
+    if (lane == 0) atomicMax(&s_xtop, top);
+    __syncthreads();
+    const int xt = s_xtop;
+    for (int i = tid; i < n; i += blockDim.x) xs[i] = fx_limbs(fx_of(xb[i], xt));
+    __syncthreads();
+  }
+  const int xtop = s_xtop;
+  long long* out = a.part + (size_t)blockIdx.x * (2 * n + 4);
+  const uint32_t tile_bytes = (uint32_t)(stage_elems * sizeof(int2));
+
+  if (warp == kFxRW + kFxCW) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      prefetch_tmap(&map);
+      int k = 0;
+      for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+        const int s = k % S;
+        if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1, gtimer() + a.wait_ns)) {
+          atomicOr(a.status, LS_DEV_TIMEOUT);
+          break;
+        }
+        if (blockIdx.x == 0 && k == a.inject_skip) continue;   // test hook: this tile never arrives
+        mbar_arrive_expect_tx(&full[s], tile_bytes);
+        int2* dst = tiles + (size_t)s * stage_elems;
+        for (int q = 0; q < nbox; ++q) tma_load_2d(dst + (size_t)q * tr * boxw, &map, q * boxw, t * tr, &full[s]);
+      }
+      // drain: every issued copy lands before the CTA can exit
+      const int issued = k;
+      for (int kk = max(0, issued - S); kk < issued; ++kk)
+        mbar_wait_bounded(&full[kk % S], (kk / S) & 1, gtimer() + a.wait_ns);
+    }
+    return;
+  }
+
+  if (warp < kFxRW) {
+    // ------------------------------------------------------------ row warps
+    // lane (rl, q) of warp w sums row rl over the columns rho + i CS of each
+    // box (rotated by rl so that the rows of a warp sit on different banks),
+    // in four independent accumulator sets; the lanes of a row are combined
+    // by shuffles and each warp's row partials go to the epilogue warp.
+    const int LPR = 32 / tr, CS = kFxRW * LPR;
+    const int rl = lane / LPR, q = lane - rl * LPR;
+    const int rho = LPR * ((warp + rl) % kFxRW) + q;
+    int k = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+      const int s = k % S, slot = k & 1;
+      bool ok = mbar_wait_bounded(&full[s], (k / S) & 1, gtimer() + a.wait_ns);
+      if (ok && k >= 2) ok = mbar_wait_bounded(&pfree[slot], ((k >> 1) - 1) & 1, gtimer() + a.wait_ns);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicOr(a.status, LS_DEV_TIMEOUT);
+        break;
+      }
+      const int2* tl = tiles + (size_t)s * stage_elems;
+      const int64_t row0 = (int64_t)t * tr;
+      const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
+      int64_t T2[4] = {0, 0, 0, 0}, T1[4] = {0, 0, 0, 0}, T0[4] = {0, 0, 0, 0};
+      if (rl < rows) {
+        for (int qb = 0; qb < nbox; ++qb) {
+          const int2* bp = tl + (size_t)qb * tr * pitch + rl * pitch;
+          const int2* xp = xs + qb * 256;
+          const int w = (nbox == 1) ? n : min(256, n - qb * 256);
+          int c = rho;
+          for (; c + 3 * CS < w; c += 4 * CS) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int2 av = bp[c + u * CS];
+              const int2 xv = xp[c + u * CS];
+              T2[u] = mad_wide(av.y, xv.y, T2[u]);
+              T1[u] = mad_wide(av.y, xv.x, T1[u]);
+              T1[u] = mad_wide(av.x, xv.y, T1[u]);
+              T0[u] = mad_wide(av.x, xv.x, T0[u]);
+            }
+          }
+          for (; c < w; c += CS) {
+            const int2 av = bp[c];
+            const int2 xv = xp[c];
+            T2[0] = mad_wide(av.y, xv.y, T2[0]);
+            T1[0] = mad_wide(av.y, xv.x, T1[0]);
+            T1[0] = mad_wide(av.x, xv.y, T1[0]);
+            T0[0] = mad_wide(av.x, xv.x, T0[0]);
+          }
+        }
+      }
+      // the four sets hold disjoint subsets of the lane's <= 64 columns, so
+      // their sums keep the per-lane bounds
+      const int64_t S2 = (T2[0] + T2[1]) + (T2[2] + T2[3]);
+      const int64_t S1 = (T1[0] + T1[1]) + (T1[2] + T1[3]);
+      const int64_t S0 = (T0[0] + T0[1]) + (T0[2] + T0[3]);
+      __int128 V = ((__int128)S2 << 56) + ((__int128)S1 << 28) + (__int128)S0;
+      for (int o = LPR >> 1; o > 0; o >>= 1) V += shfl_xor_i128(V, o);
+      if (q == 0) p1[((size_t)slot * kFxRW + warp) * tr + rl] = V;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pready[slot]);
+    }
+    return;
+  }
+
+  if (warp == kFxRW + kFxCW + 1) {
+    // ------------------------------------------------------------ epilogue warp
+    // lane r finishes row r of each tile: the exact row dot (the four warps'
+    // partials in warp order), r_j = b_j - (A x)_j, the squared norms, and
+    // r_j 2^(e_j - 1077) in fixed point at the CTA's running exponent, handed
+    // to the column group with the shift its sums need first.
+    double rn2 = 0.0, dn2 = 0.0;
+    int Ecta = kNoExp, bad = 0;
+    // the row scalars (b, e_j, r_prev) of the next tile are loaded one tile
+    // ahead, so their global-memory latency is not on the hand-off path
+    double nb = 0.0, nrp = 0.0;
+    int ne = 0;
+    auto load_next = [&](int tn) {
+      nb = 0.0; nrp = 0.0; ne = 0;
+      if (tn < a.ntiles) {
+        const int64_t r0 = (int64_t)tn * tr;
+        if (r0 + lane < a.m && lane < tr) {
+          nb = a.b[r0 + lane];
+          ne = a.rexp[r0 + lane];
+          if (a.r_prev) nrp = a.r_prev[r0 + lane];
+        }
+      }
+    };
+    load_next(blockIdx.x);
+    int k = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+      const int s = k % S, slot = k & 1;
+      const int64_t row0 = (int64_t)t * tr;
+      const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
+      const double bj = nb, rpj = nrp;
+      const int ej = ne;
+      load_next(t + gridDim.x);
+      bool ok = mbar_wait_bounded(&pready[slot], (k >> 1) & 1, gtimer() + a.wait_ns);
+      if (ok && k >= S) ok = mbar_wait_bounded(&rfree[s], ((k / S) - 1) & 1, gtimer() + a.wait_ns);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicOr(a.status, LS_DEV_TIMEOUT);
+        break;
+      }
+      uint64_t rbits = 0;
+      int qj = kNoExp;
+      if (lane < rows) {
+        __int128 Sj = 0;
+#pragma unroll
+        for (int w = 0; w < kFxRW; ++w) Sj += p1[((size_t)slot * kFxRW + w) * tr + lane];
+        const double ax = scale2(i128_to_double(Sj), ej + xtop - 2154);
+        const double rj = bj - ax;
+        rn2 += rj * rj;
+        if (a.r_prev) { const double dl = rj - rpj; dn2 += dl * dl; }
+        if (a.r_out) a.r_out[row0 + lane] = rj;
+        rbits = (uint64_t)__double_as_longlong(rj);
+        const int e = (int)((rbits >> 52) & 0x7FF);
+        if (e == 0x7FF) bad = 1;
+        else if (rj != 0.0) qj = (e ? e : 1) + ej;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pfree[slot]);
+      const int Enew = max(Ecta, warp_max_int(qj));
+      const int shift = (Ecta == kNoExp || Enew == kNoExp) ? 0 : Enew - Ecta;
+      Ecta = Enew;
+      if (lane < tr) {
+        int64_t P = 0;
+        if (qj != kNoExp) {
+          uint64_t M;
+          int be;
+          fx_decode(rbits, M, be);
+          P = fx_round_shift(M, qj - Ecta + 2);
+          if (rbits >> 63) P = -P;
+        }
+        rslot[s * tr + lane] = fx_limbs(P);
+      }
+      if (lane == 0) rshift[s] = shift;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rready[s]);
+    }
+    rn2 = warp_sum(rn2);
+    dn2 = warp_sum(dn2);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      out[2 * n] = (long long)Ecta;
+      out[2 * n + 1] = __double_as_longlong(rn2);
+      out[2 * n + 2] = __double_as_longlong(dn2);
+      out[2 * n + 3] = s_xbad | (bad ? 2 : 0);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- column group
+  const int tc = tid - kFxRW * 32;
+  constexpr int kCT = kFxCW * 32;
+  int64_t T2[NPT2], T1[NPT2], T0[NPT2];
+  __int128 W[NPT2];
+  int off[NPT2];                                 // element offset of (row 0, column) in a stage
+#pragma unroll
+  for (int u = 0; u < NPT2; ++u) {
+    T2[u] = 0; T1[u] = 0; T0[u] = 0; W[u] = 0;
+    const int c = tc + kCT * u;
+    off[u] = (nbox == 1) ? c : ((c >> 8) * (tr * 256) + (c & 255));
+  }
+  int since = 0;
+  auto fold = [&]() {
+#pragma unroll
+    for (int u = 0; u < NPT2; ++u) {
+      W[u] += ((__int128)T2[u] << 28) + (__int128)T1[u] + (__int128)(T0[u] >> 28);
+      T2[u] = 0; T1[u] = 0; T0[u] = 0;
+    }
+  };
+  int k = 0;
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+    const int s = k % S;
+    bool ok = mbar_wait_bounded(&full[s], (k / S) & 1, gtimer() + a.wait_ns);
+    if (ok) ok = mbar_wait_bounded(&rready[s], (k / S) & 1, gtimer() + a.wait_ns);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) atomicOr(a.status, LS_DEV_TIMEOUT);
+      break;
+    }
+    const int2* tl = tiles + (size_t)s * stage_elems;
+    const int2* rs = rslot + s * tr;
+    const int64_t row0 = (int64_t)t * tr;
+    const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
+    const int sh = rshift[s];
+    if (sh > 0) {                      // a larger exponent arrived: realign the sums
+      fold();
+      since = 0;
+#pragma unroll
+      for (int u = 0; u < NPT2; ++u) W[u] = (sh >= 120) ? (__int128)0 : (W[u] >> sh);
+    }
+    for (int r = 0; r < rows; ++r) {
+      const int2 pv = rs[r];
+      const int2* rowp = tl + r * pitch;
+#pragma unroll
+      for (int u = 0; u < NPT2; ++u) {
+        if (tc + kCT * u < n) {
+          const int2 av = rowp[off[u]];
+          T2[u] = mad_wide(av.y, pv.y, T2[u]);
+          T1[u] = mad_wide(av.y, pv.x, T1[u]);
+          T1[u] = mad_wide(av.x, pv.y, T1[u]);
+          T0[u] = mad_wide(av.x, pv.x, T0[u]);
+        }
+      }
+    }
+    since += rows;
+    if (since + tr > kFxFoldRows) { fold(); since = 0; }
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&rfree[s]);
+      mbar_arrive(&empty[s]);
+    }
+  }
+  fold();
+#pragma unroll
+  for (int u = 0; u < NPT2; ++u) {
+    const int c = tc + kCT * u;
+    if (c < n) {
+      out[2 * c] = (long long)(unsigned long long)W[u];
+      out[2 * c + 1] = (long long)(W[u] >> 64);
+    }
+  }
+}
+
+// Sum the per-CTA fixed-point partials exactly (aligned to the largest CTA
+// exponent) and round once: c[k] = 2^(E - 2126) sum_p W_kp; the squared norms
+// are FP64 sums in CTA order.  Writes c (n) and norms (2); a non-finite x or
+// r in any CTA makes c and norms NaN.
+__global__ void k_fx_reduce(const long long* __restrict__ part, int nparts, int n, double* __restrict__ c,
+                            double* __restrict__ norms, const IterState* st) {
+  if (st && st->done) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n + 2) return;
+  const size_t stride = 2 * (size_t)n + 4;
+  int flags = 0;
+  for (int p = 0; p < nparts; ++p) flags |= (int)part[p * stride + 2 * n + 3];
+  if (k >= n) {
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += __longlong_as_double(part[p * stride + 2 * n + 1 + (k - n)]);
+    norms[k - n] = flags ? __longlong_as_double(0x7FF8000000000000ll) : s;
+    return;
+  }
+  int E = kNoExp;
+  for (int p = 0; p < nparts; ++p) E = max(E, (int)part[p * stride + 2 * n]);
+  __int128 sum = 0;
+  if (E != kNoExp) {
+    for (int p = 0; p < nparts; ++p) {
+      const int Ep = (int)part[p * stride + 2 * n];
+      if (Ep == kNoExp) continue;
+      const int sh = E - Ep;
+      if (sh >= 120) continue;
+      const __int128 w = ((__int128)part[p * stride + 2 * k + 1] << 64) |
+                         (__int128)(unsigned long long)part[p * stride + 2 * k];
+      sum += w >> sh;
+    }
+  }
+  double v = (E == kNoExp) ? 0.0 : scale2(i128_to_double(sum), E - 2126);
+  if (flags) v = __longlong_as_double(0x7FF8000000000000ll);
+  c[k] = v;
+}
+
+// ------------------------------------------------------------------ host side
+FxGeom fx_geometry(const ls_ctx* ctx, int64_t n, int64_t m) {
+  FxGeom g;
+  if (n <= 256) {
+    g.boxw = (int)((n + 1) & ~1LL);
+    g.nbox = 1;
+    g.tr = 32;
+  } else {
+    g.boxw = 256;
+    g.nbox = (int)((n + 255) / 256);
+    g.tr = (g.nbox <= 2) ? 16 : 8;
+  }
+  const size_t stage = (size_t)g.tr * g.nbox * g.boxw * sizeof(int2);
+  g.stages = (int)std::max<size_t>(2, std::min<size_t>(4, (192 * 1024) / stage));
+  const int64_t ntiles = (m + g.tr - 1) / g.tr;
+  g.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ntiles));
+  g.smem = g.stages * stage + (size_t)2 * kFxRW * g.tr * 16 + (size_t)((n + 1) & ~1LL) * 8 +
+           (size_t)g.stages * g.tr * 8 + (size_t)((g.stages + 1) & ~1) * 4 + (4 * (size_t)g.stages + 4) * 8 + 128;
+  return g;
+}
+
+size_t fx_part_words(const FxGeom& g, int64_t n) { return (size_t)g.grid * (2 * (size_t)n + 4); }
+
+cudaError_t launch_to_fixed(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, int2* Af, int64_t ldf,
+                            int* rexp) {
+  const int64_t blocks = (m + 7) / 8;
+  k_to_fixed<<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, m, (int)n, lda, Af, ldf, rexp, ctx->d_status);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+typedef CUresult (*FxEncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t make_fx_tensor_map(ls_ctx* ctx, CUtensorMap* map, const int2* Af, int64_t m, int64_t n, int64_t ldf,
+                               const FxGeom& g) {
+  if (!ctx->encode_tiled) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    ctx->encode_tiled = fn;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)ldf * sizeof(int2)};
+  cuuint32_t box[2] = {(cuuint32_t)g.boxw, (cuuint32_t)g.tr};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = ((FxEncodeTiledFn)ctx->encode_tiled)(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, (void*)Af, dims, strides,
+                                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int NPT2>
+static cudaError_t launch_fx_t(ls_ctx* ctx, const CUtensorMap& map, const FxGeom& g, const FxArgs& a) {
+  cudaError_t e = cudaFuncSetAttribute(k_fx_pass<NPT2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+  if (e != cudaSuccess) return e;
+  k_fx_pass<NPT2><<<g.grid, kFxThreads, g.smem, ctx->stream>>>(map, a);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fx_pass(ls_ctx* ctx, const CUtensorMap& map, const FxGeom& g, int64_t m, int64_t n,
+                           const int* rexp, const double* b, const double* x, const double* r_prev, double* r_out,
+                           long long* part, const IterState* st) {
+  FxArgs a;
+  a.m = m; a.n = (int)n; a.boxw = g.boxw; a.nbox = g.nbox; a.tr = g.tr; a.stages = g.stages;
+  a.ntiles = (int)((m + g.tr - 1) / g.tr);
+  a.rexp = rexp; a.b = b; a.x = x; a.r_prev = r_prev; a.r_out = r_out; a.part = part; a.st = st;
+  a.status = ctx->d_status;
+  a.wait_ns = ctx->wait_ns;
+  a.inject_skip = ctx->inject_skip_tile;
+  ctx->inject_skip_tile = -1;                       // one-shot
+  const int npt2 = (int)((n + kFxCW * 32 - 1) / (kFxCW * 32));
+  if (npt2 <= 1) return launch_fx_t<1>(ctx, map, g, a);
+  if (npt2 <= 2) return launch_fx_t<2>(ctx, map, g, a);
+  if (npt2 <= 4) return launch_fx_t<4>(ctx, map, g, a);
+  if (npt2 <= 8) return launch_fx_t<8>(ctx, map, g, a);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fx_reduce(ls_ctx* ctx, const long long* part, int nparts, int64_t n, double* c, double* norms,
+                             const IterState* st) {
+  const int threads = 128;
+  const int grid = (int)((n + 2 + threads - 1) / threads);
+  k_fx_reduce<<<grid, threads, 0, ctx->stream>>>(part, nparts, (int)n, c, norms, st);
+  ++ctx->launches;
+  return cudaGetLastError();
+}
+
+}  // namespace lsk

@@ -6,9 +6,11 @@
 // k_fused_pass (a6): persistent, one CTA per SM.  A is streamed in row tiles
 // (tr rows x all columns) by TMA (cp.async.bulk.tensor.2d) into a ring of
 // shared-memory stages fed by one producer warp; eight consumer warps use each
-// tile twice -- first each warp forms the row dots A_j x (lanes over columns,
-// warp-shuffle tree) and r_j = b_j - A_j x, then every thread adds r_j A_jk to
-// its own columns of c -- so A is read from HBM exactly once per pass.  Each
+// tile twice -- first the row dots A_j x (for n >= 32 every warp takes a
+// rotated slice of every row's columns, a few lanes per row combined by two
+// shuffles and the eight warps summed in warp order; for n < 32 a warp per
+// row) and r_j = b_j - A_j x, then every thread adds r_j A_jk to its own
+// columns of c -- so A is read from HBM exactly once per pass.  Each
 // CTA writes one partial (c, ||r||^2, ||r - r_prev||^2); partials are summed
 // over CTAs in index order by the next kernel, so results are bit-identical
 // run to run.  Every wait is bounded by %globaltimer.

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <climits>
 #include <string>
 #include <vector>
 
@@ -355,6 +357,12 @@ struct ls_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_done = nullptr;
   cudaEvent_t piece_done[4] = {nullptr, nullptr, nullptr, nullptr};   // host A uploaded piece by piece
+  // bounded device waits of the fixed-point pass give up after this long
+  unsigned long long wait_ns = LS_WAIT_NS;
+  // failure injection for tests (ls_inject_fault): the next fixed-point pass's
+  // CTA 0 skips this tile (-1: none); the next device allocation fails (0: none)
+  int inject_skip_tile = -1;
+  int inject_alloc_fail = 0;
 };
 
 // ------------------------------------------------------------ launch helpers
@@ -459,6 +467,25 @@ cudaError_t launch_sp_pass(ls_ctx* ctx, int64_t m, int64_t n, const int64_t* arp
                            const double* aval, const double* b, const double* x, double* r, const int64_t* col_ptr,
                            const int32_t* crow, const double* cval, double* norms_part, double* cpart, double* out,
                            const IterState* st);
+
+// fixed-point fused pass (fxpass.cu)
+struct FxGeom {
+  int boxw, nbox, tr, stages;
+  size_t smem;
+  int grid;
+};
+FxGeom fx_geometry(const ls_ctx* ctx, int64_t n, int64_t m);
+size_t fx_part_words(const FxGeom& g, int64_t n);
+constexpr int64_t kFxMaxN = 1024;
+cudaError_t launch_to_fixed(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, int2* Af, int64_t ldf,
+                            int* rexp);
+cudaError_t make_fx_tensor_map(ls_ctx* ctx, CUtensorMap* map, const int2* Af, int64_t m, int64_t n, int64_t ldf,
+                               const FxGeom& g);
+cudaError_t launch_fx_pass(ls_ctx* ctx, const CUtensorMap& map, const FxGeom& g, int64_t m, int64_t n,
+                           const int* rexp, const double* b, const double* x, const double* r_prev, double* r_out,
+                           long long* part, const IterState* st);
+cudaError_t launch_fx_reduce(ls_ctx* ctx, const long long* part, int nparts, int64_t n, double* c, double* norms,
+                             const IterState* st);
 
 // batched path (batched.cu)
 // One problem of a batched solve or one server slot: caller's arrays, sizes,

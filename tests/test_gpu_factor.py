@@ -49,7 +49,10 @@ def run_factor(env, Bo, seed=0):
 @pytest.mark.parametrize("m,n,kappa,res,d", [(4000, 50, 1e10, 1e-6, 1000), (4000, 50, 10.0, 1e-3, 1000),
                                              (2000, 1, 1.0, 1e-2, 20), (3000, 33, 1e6, 1e-8, 660),
                                              (20000, 257, 1e4, 1e-4, 5140), (500, 5, 1e2, 1e-1, 10),
-                                             (100000, 40, 1e6, 1e-6, 70000), (120000, 12, 1e3, 1e-4, 100000)])
+                                             (100000, 40, 1e6, 1e-6, 70000), (120000, 12, 1e3, 1e-4, 100000),
+                                             # n = 720: 23 column groups of 32, so the lookahead factors its
+                                             # panels with 2 warps (>= 20 groups left), then 4 (>= 10), then 8
+                                             (30000, 720, 1e3, 1e-4, 14000)])
 def test_factor_parity(env, m, n, kappa, res, d):
     P = problems.make_problem(m, n, kappa, res, n)
     Bo = oracle.sketch(P["A"], P["b"], d, 8, 0)
@@ -61,7 +64,9 @@ def test_factor_parity(env, m, n, kappa, res, d):
     kB = np.linalg.cond(Bm)
     # upper triangular, backward stable
     assert np.all(np.tril(Rg, -1) == 0.0)
-    L = np.longdouble
+    # (extended precision where affordable; in FP64 the check's own rounding,
+    # at most d u ||B||^2, is 1/(10 n) of the bound)
+    L = np.longdouble if d * n * n < 2e9 else np.float64
     err = np.max(np.abs(Rg.astype(L).T @ Rg.astype(L) - Bm.astype(L).T @ Bm.astype(L)))
     assert err <= 10 * d * n * U * nB ** 2
     # R vs oracle R up to row signs

@@ -31,7 +31,11 @@ def env():
 
 PASS_CASES = [(4000, 50, 50), (1, 1, 2), (7, 3, 4), (1000, 17, 18), (999, 31, 32), (1003, 32, 32),
               (1001, 33, 34), (2049, 64, 64), (3000, 100, 100), (5001, 257, 258), (4000, 300, 300),
-              (3007, 1000, 1000), (2000, 513, 514), (2100, 2048, 2048), (300, 255, 256), (130, 128, 128)]
+              (3007, 1000, 1000), (2000, 513, 514), (2100, 2048, 2048), (300, 255, 256), (130, 128, 128),
+              # many tiles per CTA (the launch geometry of the large workload): at m = 200,000 every CTA
+              # of the persistent pass takes 11 (n = 50), 55 (n = 200) or 164 (n = 1000) tiles, so the
+              # tile ring and the r hand-off ring wrap many times and partials accumulate over tiles
+              (200_000, 50, 50), (200_000, 200, 200), (200_001, 1000, 1000)]
 
 
 @pytest.mark.parametrize("m,n,lda", PASS_CASES)
@@ -167,6 +171,47 @@ def test_solve_small_config_forward_error(env, kappa, res):
     assert abs(info.iters - io["iters"]) <= 5
     assert info.normest == pytest.approx(io["normest"], rel=1e-10)
     assert info.condest == pytest.approx(io["condest"], rel=1e-6)
+
+
+@pytest.mark.parametrize("extra", [0, 2])
+def test_stopping_rule_fires_at_the_predicted_step(env, extra):
+    """The Sec. 3.3 rule on a problem whose iterates are exact in FP64: A =
+    [I_2; 0], b = e_1, R = I, alpha = 1/2 from x_0 = 0 gives r(x_i) = 2^-i e_1.
+    With gamma = 1, normest = 2^10, rho = 0 the rule first holds at i = 44
+    (the oracle's pin, tests/test_oracle_lsq.py), and x_44 is returned after
+    `extra` more updates -- the same step and bits on the GPU."""
+    torch, ls, ctx = env
+    m, n = 8, 2
+    A = np.zeros((m, n)); A[:n, :n] = np.eye(n)
+    b = np.zeros(m); b[0] = 1.0
+    R = dev(torch, np.eye(n).ravel(order="F"))
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    opts = ls.default_opts()
+    opts.gamma, opts.rho, opts.alpha, opts.extra_iters = 1.0, 0.0, 0.5, extra
+    info = ls.ls_info()
+    info.normest, info.condest = 1024.0, 1.0
+    st, it = ctx.ls_iterate(dev(torch, A), m, n, n, dev(torch, b), R, n, x, 100, opts, info)
+    assert st == ls.LS_OK and it.stop_reason == 0 and it.iters == 44 + extra, (st, it.iters)
+    xh = host(x)
+    assert xh[0] == 1.0 - 2.0 ** -(44 + extra) and xh[1] == 0.0
+    assert it.step_norm == 2.0 ** -(44 + extra)
+
+
+def test_solve_headline_shape_forward_error(env):
+    """The whole method at the large workload's shape and launch configuration
+    (n = 1000, d = 20 n, zeta = 8, kappa = 1e8, ||r|| = 1e-4) on m = 200,000
+    rows: the rule held, and the forward error is within 10x that of a
+    Householder-QR solve of the same problem (the acceptance rule; Thm 4.1)."""
+    torch, ls, ctx = env
+    m, n, d = 200_000, 1000, 20_000
+    P = problems.make_problem_torch(m, n, 1e8, 1e-4, 11, device="cuda")
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    st, info = ctx.ls_solve(P["A"], P["b"], m, n, n, d, 8, 100, 0, x)
+    xt = host(P["x"])
+    fe = oracle.forward_error(host(x), xt)
+    fe_qr = oracle.forward_error(oracle.qr_solve_lapack(host(P["A"]), host(P["b"])), xt)
+    assert st == ls.LS_OK and info.stop_reason == 0, (st, info.stop_reason, info.iters)
+    assert fe <= 10 * fe_qr, (fe, fe_qr, info.iters)
 
 
 def test_solve_deterministic_and_host_pointers(env):
