@@ -92,6 +92,7 @@ __device__ __forceinline__ int2 fx_limbs(int64_t F) {
   return make_int2((int)(F & 0x0FFFFFFF), (int)(F >> 28));
 }
 
+// c + a b, 32 x 32 -> 64-bit signed (one IMAD.WIDE).
 __device__ __forceinline__ int64_t mad_wide(int a, int b, int64_t c) {
   int64_t d;
   asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
@@ -122,6 +123,25 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
   const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
   const long long hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
   return ((__int128)hi2 << 64) | (__int128)lo2;
+}
+
+// Bounded wait for the phase with the given parity.  try_wait carries a
+// suspend-time hint, so a waiting warp is parked by the hardware until the
+// phase completes (or the hint runs out) instead of spinning: spinning
+// waiters took issue slots and shared-memory bandwidth from the warps doing
+// the work on the same sub-partition.  False once `ns` have passed.
+__device__ __forceinline__ bool fx_wait(uint64_t* bar, uint32_t parity, unsigned long long ns) {
+  const uint64_t deadline = gtimer() + ns;
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    if (ok) return true;
+    if (gtimer() > deadline) return false;
+  }
 }
 
 __device__ __forceinline__ int warp_max_int(int v) {
@@ -234,7 +254,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
       int k = 0;
       for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
         const int s = k % S;
-        if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1, gtimer() + a.wait_ns)) {
+        if (k >= S && !fx_wait(&empty[s], ((k / S) - 1) & 1, a.wait_ns)) {
           atomicOr(a.status, LS_DEV_TIMEOUT);
           break;
         }
@@ -246,7 +266,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
       // drain: every issued copy lands before the CTA can exit
       const int issued = k;
       for (int kk = max(0, issued - S); kk < issued; ++kk)
-        mbar_wait_bounded(&full[kk % S], (kk / S) & 1, gtimer() + a.wait_ns);
+        fx_wait(&full[kk % S], (kk / S) & 1, a.wait_ns);
     }
     return;
   }
@@ -263,8 +283,8 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
     int k = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
       const int s = k % S, slot = k & 1;
-      bool ok = mbar_wait_bounded(&full[s], (k / S) & 1, gtimer() + a.wait_ns);
-      if (ok && k >= 2) ok = mbar_wait_bounded(&pfree[slot], ((k >> 1) - 1) & 1, gtimer() + a.wait_ns);
+      bool ok = fx_wait(&full[s], (k / S) & 1, a.wait_ns);
+      if (ok && k >= 2) ok = fx_wait(&pfree[slot], ((k >> 1) - 1) & 1, a.wait_ns);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) atomicOr(a.status, LS_DEV_TIMEOUT);
         break;
@@ -279,15 +299,28 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
           const int2* xp = xs + qb * 256;
           const int w = (nbox == 1) ? n : min(256, n - qb * 256);
           int c = rho;
+          for (; c + 7 * CS < w; c += 8 * CS) {          // eight columns: all loads, then the products
+            int2 av[8], xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { av[u] = bp[c + u * CS]; xv[u] = xp[c + u * CS]; }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              T2[u & 3] = mad_wide(av[u].y, xv[u].y, T2[u & 3]);
+              T1[u & 3] = mad_wide(av[u].y, xv[u].x, T1[u & 3]);
+              T1[u & 3] = mad_wide(av[u].x, xv[u].y, T1[u & 3]);
+              T0[u & 3] = mad_wide(av[u].x, xv[u].x, T0[u & 3]);
+            }
+          }
           for (; c + 3 * CS < w; c += 4 * CS) {
+            int2 av[4], xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { av[u] = bp[c + u * CS]; xv[u] = xp[c + u * CS]; }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const int2 av = bp[c + u * CS];
-              const int2 xv = xp[c + u * CS];
-              T2[u] = mad_wide(av.y, xv.y, T2[u]);
-              T1[u] = mad_wide(av.y, xv.x, T1[u]);
-              T1[u] = mad_wide(av.x, xv.y, T1[u]);
-              T0[u] = mad_wide(av.x, xv.x, T0[u]);
+              T2[u] = mad_wide(av[u].y, xv[u].y, T2[u]);
+              T1[u] = mad_wide(av[u].y, xv[u].x, T1[u]);
+              T1[u] = mad_wide(av[u].x, xv[u].y, T1[u]);
+              T0[u] = mad_wide(av[u].x, xv[u].x, T0[u]);
             }
           }
           for (; c < w; c += CS) {
@@ -346,8 +379,8 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
       const double bj = nb, rpj = nrp;
       const int ej = ne;
       load_next(t + gridDim.x);
-      bool ok = mbar_wait_bounded(&pready[slot], (k >> 1) & 1, gtimer() + a.wait_ns);
-      if (ok && k >= S) ok = mbar_wait_bounded(&rfree[s], ((k / S) - 1) & 1, gtimer() + a.wait_ns);
+      bool ok = fx_wait(&pready[slot], (k >> 1) & 1, a.wait_ns);
+      if (ok && k >= S) ok = fx_wait(&rfree[s], ((k / S) - 1) & 1, a.wait_ns);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) atomicOr(a.status, LS_DEV_TIMEOUT);
         break;
@@ -405,12 +438,16 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
   constexpr int kCT = kFxCW * 32;
   int64_t T2[NPT2], T1[NPT2], T0[NPT2];
   __int128 W[NPT2];
-  int off[NPT2];                                 // element offset of (row 0, column) in a stage
+  // element offset of (row 0, column) in a stage.  Columns past n still read
+  // inside the stage (the TMA zero-filled box columns, or the row's last
+  // column when one box holds the row), so the loads need no branch; their
+  // sums are never written out.
+  int off[NPT2];
 #pragma unroll
   for (int u = 0; u < NPT2; ++u) {
     T2[u] = 0; T1[u] = 0; T0[u] = 0; W[u] = 0;
     const int c = tc + kCT * u;
-    off[u] = (nbox == 1) ? c : ((c >> 8) * (tr * 256) + (c & 255));
+    off[u] = (nbox == 1) ? min(c, boxw - 1) : ((c >> 8) * (tr * 256) + (c & 255));
   }
   int since = 0;
   auto fold = [&]() {
@@ -423,8 +460,8 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
   int k = 0;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
     const int s = k % S;
-    bool ok = mbar_wait_bounded(&full[s], (k / S) & 1, gtimer() + a.wait_ns);
-    if (ok) ok = mbar_wait_bounded(&rready[s], (k / S) & 1, gtimer() + a.wait_ns);
+    bool ok = fx_wait(&full[s], (k / S) & 1, a.wait_ns);
+    if (ok) ok = fx_wait(&rready[s], (k / S) & 1, a.wait_ns);
     if (!__all_sync(0xffffffffu, ok)) {
       if (lane == 0) atomicOr(a.status, LS_DEV_TIMEOUT);
       break;
@@ -443,15 +480,15 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
     for (int r = 0; r < rows; ++r) {
       const int2 pv = rs[r];
       const int2* rowp = tl + r * pitch;
+      int2 av[NPT2];
+#pragma unroll
+      for (int u = 0; u < NPT2; ++u) av[u] = rowp[off[u]];     // all loads first
 #pragma unroll
       for (int u = 0; u < NPT2; ++u) {
-        if (tc + kCT * u < n) {
-          const int2 av = rowp[off[u]];
-          T2[u] = mad_wide(av.y, pv.y, T2[u]);
-          T1[u] = mad_wide(av.y, pv.x, T1[u]);
-          T1[u] = mad_wide(av.x, pv.y, T1[u]);
-          T0[u] = mad_wide(av.x, pv.x, T0[u]);
-        }
+        T2[u] = mad_wide(av[u].y, pv.y, T2[u]);
+        T1[u] = mad_wide(av[u].y, pv.x, T1[u]);
+        T1[u] = mad_wide(av[u].x, pv.y, T1[u]);
+        T0[u] = mad_wide(av[u].x, pv.x, T0[u]);
       }
     }
     since += rows;

@@ -91,13 +91,14 @@ __global__ void __launch_bounds__(1024, 1) k_rate(int iters, uint32_t seed, unsi
 }
 
 template <int OP>
-int run_one(int sms, int iters, unsigned long long* d_cyc, uint32_t* d_sink, double* rate_clk, double* rate_ns) {
+int run_one(int sms, int iters, unsigned long long* d_cyc, uint32_t* d_sink, double* rate_clk, double* rate_ns,
+            int threads = 1024) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  k_rate<OP><<<sms, 1024>>>(8, 1u, d_cyc, d_sink);   // warm-up
+  k_rate<OP><<<sms, threads>>>(8, 1u, d_cyc, d_sink);   // warm-up
   cudaEventRecord(e0);
-  k_rate<OP><<<sms, 1024>>>(iters, 1u, d_cyc, d_sink);
+  k_rate<OP><<<sms, threads>>>(iters, 1u, d_cyc, d_sink);
   cudaEventRecord(e1);
   if (cudaEventSynchronize(e1) != cudaSuccess) return 1;
   float ms = 0.f;
@@ -108,7 +109,7 @@ int run_one(int sms, int iters, unsigned long long* d_cyc, uint32_t* d_sink, dou
   for (int i = 0; i < sms; ++i) cyc += (double)h[i];
   cyc /= sms;
   delete[] h;
-  const double ops_per_cta = 1024.0 * 8.0 * iters * kOpsPerStep[OP];
+  const double ops_per_cta = (double)threads * 8.0 * iters * kOpsPerStep[OP];
   *rate_clk = ops_per_cta / cyc;
   *rate_ns = ops_per_cta * sms / (ms * 1e6);
   cudaEventDestroy(e0);
@@ -138,11 +139,28 @@ extern "C" __attribute__((visibility("default"))) int ls_probe_rates(char* out, 
   if (cudaMalloc(&d_sink, sizeof(uint32_t) * 1024 * sms) != cudaSuccess) return 1;
   double rc[kNumOps] = {0}, rn[kNumOps] = {0};
   int err = run_upto<kNumOps - 1>(sms, iters, d_cyc, d_sink, rc, rn);
+  // the same forms with fewer warps per SM (one CTA of 128, 256, 512 threads):
+  // what a kernel with 1, 2 or 4 warps per sub-partition issuing them gets
+  const int occ[3] = {128, 256, 512};
+  double wide[3], ffma[3], dfma[3];
+  for (int i = 0; i < 3; ++i) {
+    double dummy;
+    err |= run_one<kImadWide>(sms, iters, d_cyc, d_sink, &wide[i], &dummy, occ[i]);
+    err |= run_one<kFfma>(sms, iters, d_cyc, d_sink, &ffma[i], &dummy, occ[i]);
+    err |= run_one<kDfma>(sms, iters, d_cyc, d_sink, &dfma[i], &dummy, occ[i]);
+  }
   cudaFree(d_cyc);
   cudaFree(d_sink);
   int pos = snprintf(out, out_len, "{\"sms\": %d, \"iters\": %d, \"rates\": {", sms, iters);
   for (int i = 0; i < kNumOps && pos < out_len; ++i)
     pos += snprintf(out + pos, out_len - pos, "%s\"%s\": [%.3f, %.2f]", i ? ", " : "", kNames[i], rc[i], rn[i]);
-  if (pos < out_len) snprintf(out + pos, out_len - pos, "}}");
+  if (pos < out_len)
+    pos += snprintf(out + pos, out_len - pos,
+                    "}, \"by_threads_per_sm\": {\"threads\": [128, 256, 512, 1024], "
+                    "\"imad_wide_s32\": [%.3f, %.3f, %.3f, %.3f], \"ffma\": [%.3f, %.3f, %.3f, %.3f], "
+                    "\"dfma\": [%.3f, %.3f, %.3f, %.3f]}",
+                    wide[0], wide[1], wide[2], rc[kImadWide], ffma[0], ffma[1], ffma[2], rc[kFfma], dfma[0], dfma[1],
+                    dfma[2], rc[kDfma]);
+  if (pos < out_len) snprintf(out + pos, out_len - pos, "}");
   return err;
 }
