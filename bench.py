@@ -148,6 +148,9 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- oracle timing
+_SAMPLE_CACHE: dict = {}
+
+
 def _oracle_sample(iters_hint):
     """One bounded sample of the oracle on the large workload (single thread):
       sketch     : oracle sketch of the first m_s = 50,000 rows (d = 20000), x m/m_s
@@ -166,7 +169,11 @@ def _oracle_sample(iters_hint):
     w0 = time.perf_counter()
     m, n, d, zeta = CFG["m"], CFG["n"], CFG["d"], CFG["zeta"]
     ms_rows, dq = 50_000, 2000
-    P = problems.make_problem(ms_rows, n, CFG["kappa"], CFG["resnorm"], 1)
+    # the sample's inputs (and the oracle's iteration count) are drawn once
+    # per process; only the oracle's own work below is timed
+    if "P" not in _SAMPLE_CACHE:
+        _SAMPLE_CACHE["P"] = problems.make_problem(ms_rows, n, CFG["kappa"], CFG["resnorm"], 1)
+    P = _SAMPLE_CACHE["P"]
     A, b = P["A"], P["b"]
     t0 = time.perf_counter()
     oracle.sketch(A, b, d, zeta, 0)
@@ -179,9 +186,11 @@ def _oracle_sample(iters_hint):
     oracle.iterate(A, b, R, x0, 2, ne, ce, use_stop=False)
     t_it = (time.perf_counter() - t0) / 2
     if iters_hint is None:
-        Ps = problems.make_problem(20000, 100, CFG["kappa"], CFG["resnorm"], 2)
-        _, info = oracle.solve(Ps["A"], Ps["b"], 2000, zeta, CFG["q"], 0)
-        iters = info["iters"] + 1
+        if "iters" not in _SAMPLE_CACHE:
+            Ps = problems.make_problem(20000, 100, CFG["kappa"], CFG["resnorm"], 2)
+            _, info = oracle.solve(Ps["A"], Ps["b"], 2000, zeta, CFG["q"], 0)
+            _SAMPLE_CACHE["iters"] = info["iters"] + 1
+        iters = _SAMPLE_CACHE["iters"]
         how = "oracle count on m=20000, n=100"
     else:
         iters = iters_hint + 1
@@ -192,6 +201,14 @@ def _oracle_sample(iters_hint):
             f"sketch (x{d / dq:.0f}), 2 passes over {ms_rows} rows (x{scale_m:.0f} x {iters} passes, {how})")
     return est, time.perf_counter() - w0, desc, {"t_sketch_s": t_sk, "t_qr_s": t_qr, "t_pass_s": t_it,
                                                    "passes": iters}
+
+
+def _one_thread():
+    """Pool initializer: one BLAS / OpenMP thread per worker process (the
+    workers run one per core; numpy's QR in the input generator would
+    otherwise start a thread per core in every worker)."""
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
 
 
 def _oracle_sample_worker(iters_hint):
@@ -212,7 +229,7 @@ def cpu_baseline(iters_hint: int | None):
     cores = len(os.sched_getaffinity(0))
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
-    with ctx.Pool(cores) as pool:
+    with ctx.Pool(cores, initializer=_one_thread) as pool:
         res = pool.map(_oracle_sample_worker, [iters_hint] * cores)
     wall_all = time.perf_counter() - t0
     rate_all = sum(1.0 / e for e, _ in res)
@@ -533,7 +550,7 @@ def small_case(ctx, stream, args):
     xo, io = oracle.solve(P["A"], P["b"], d, c["zeta"], c["q"], c["seed"])
     t_or = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0))
-    with mp.get_context("spawn").Pool(cores) as pool:
+    with mp.get_context("spawn").Pool(cores, initializer=_one_thread) as pool:
         ts = pool.map(_oracle_small_solve_worker, range(cores))
     return {"workload": "small single FP64 problem: m=4000, n=50, kappa=1e10, ||r||=1e-6, d=20n=1000, zeta=8, "
                         "seed 0, q<=100",
@@ -999,7 +1016,7 @@ def reference_arm(args, world, rank):
     vals, walls = [], []
     desc, det = None, None
     ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
+    with ctx.Pool(cores, initializer=_one_thread) as pool:
         for i in range(args.warmup + args.steps):
             t0 = time.perf_counter()
             res = pool.map(_oracle_sample_worker, [None] * cores)

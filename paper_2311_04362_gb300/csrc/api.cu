@@ -289,6 +289,8 @@ ls_status ls_destroy(ls_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_misc) cudaFree(ctx->d_misc);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->fx_stream) cudaStreamDestroy(ctx->fx_stream);
+  if (ctx->fx_done) cudaEventDestroy(ctx->fx_done);
   if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
   for (auto& e : ctx->piece_done) if (e) cudaEventDestroy(e);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -592,9 +594,11 @@ ls_status ls_correct(ls_ctx* ctx, const double* R, int64_t ldr, int64_t n, const
   return sync_and_check(ctx);
 }
 
+// pre (may be null): A already in fixed point (ls_solve_ex converts it on a
+// second stream while the QR runs; the caller has made ctx->stream wait).
 static ls_status iterate_impl(ls_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                               const double* R, int64_t ldr, double* x, int q, const ls_opts* opts, double normest,
-                              double condest, Carve& cc, ls_info* info) {
+                              double condest, Carve& cc, ls_info* info, const FxScratch* pre = nullptr) {
   ls_opts o;
   ls_default_opts(&o);
   if (opts) o = *opts;
@@ -606,9 +610,13 @@ static ls_status iterate_impl(ls_ctx* ctx, const double* A, int64_t m, int64_t n
   FxGeom fg{};
   if (fx) {
     // A in fixed point once per call; every pass then reads the 8-byte limbs
-    fs = carve_fx(cc, ctx, m, n);
     fg = fx_geometry(ctx, n, m);
-    CUDA_TRY(ctx, launch_to_fixed(ctx, A, m, n, lda, fs.Af, fs.ldf, fs.rexp));
+    if (pre) {
+      fs = *pre;
+    } else {
+      fs = carve_fx(cc, ctx, m, n);
+      CUDA_TRY(ctx, launch_to_fixed(ctx, A, m, n, lda, fs.Af, fs.ldf, fs.rexp));
+    }
     CUDA_TRY(ctx, make_fx_tensor_map(ctx, &map, fs.Af, m, n, fs.ldf, fg));
   } else {
     CUDA_TRY(ctx, make_tensor_map(ctx, &map, A, m, n, lda, g));
@@ -1360,10 +1368,13 @@ ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int64_t m, 
   }
   if (!dx) xd = sc.take<double>((size_t)n);
 
-  // arena: B_aug, R | max(sketch, factor, iterate) scratch
+  // arena: B_aug, R, the fixed-point A (n <= 1024) | max(sketch, factor,
+  // iterate) scratch
+  const bool prefx = use_fx_pass(n);
   Carve probe(nullptr);
   probe.take<double>((size_t)d * (n + 1));
   probe.take<double>((size_t)n * n);
+  if (prefx) carve_fx(probe, ctx, m, n);
   const size_t mark = probe.off;
   carve_sketch(probe, m, d, zeta);
   size_t need = probe.off;
@@ -1373,12 +1384,13 @@ ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int64_t m, 
   probe.off = mark;
   PassGeom g = pass_geometry(ctx, n, m);
   carve_iter(probe, g, m, n);
-  if (use_fx_pass(n)) carve_fx(probe, ctx, m, n);
   need = std::max(need, probe.off);
   if ((st = ensure_arena(ctx, need))) return st;
   Carve cc(ctx->arena);
   double* B = cc.take<double>((size_t)d * (n + 1));
   double* R = cc.take<double>((size_t)n * n);
+  FxScratch pre{};
+  if (prefx) pre = carve_fx(cc, ctx, m, n);
   const size_t mark2 = cc.off;
   if ((st = reset_status(ctx))) return st;
 
@@ -1387,13 +1399,32 @@ ls_status ls_solve_ex(ls_ctx* ctx, const double* A, const double* b, int64_t m, 
   if ((st = sketch_impl(ctx, Ad, m, n, lda, bd, d, zeta, seed, B, d, cc, wait_A, dA ? nullptr : &pieces)))
     return st;
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+  if (prefx) {
+    // A to fixed point on a second stream, overlapping the QR of the sketch
+    // (the QR is bound by the FP64 unit, the conversion by memory and the
+    // integer units); the iteration waits for it
+    if (!ctx->fx_stream) {
+      CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->fx_stream, cudaStreamNonBlocking));
+      CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->fx_done, cudaEventDisableTiming));
+    }
+    CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->fx_stream, ctx->ev[1], 0));
+    if (wait_A) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->fx_stream, wait_A, 0));
+    cudaStream_t main = ctx->stream;
+    ctx->stream = ctx->fx_stream;
+    const cudaError_t ce = launch_to_fixed(ctx, Ad, m, n, lda, pre.Af, pre.ldf, pre.rexp);
+    ctx->stream = main;
+    CUDA_TRY(ctx, ce);
+    CUDA_TRY(ctx, cudaEventRecord(ctx->fx_done, ctx->fx_stream));
+  }
   cc.off = mark2;
   double est[2];
   if ((st = factor_impl(ctx, B, d, n, d, R, n, xd, seed, cc, est))) return st;
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
   cc.off = mark2;
   ls_info local{};
-  ls_status it = iterate_impl(ctx, Ad, m, n, lda, bd, R, n, xd, q, opts, est[0], est[1], cc, &local);
+  if (prefx) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->fx_done, 0));
+  ls_status it = iterate_impl(ctx, Ad, m, n, lda, bd, R, n, xd, q, opts, est[0], est[1], cc, &local,
+                              prefx ? &pre : nullptr);
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], ctx->stream));
   if (it != LS_OK && it != LS_ENOTCONV) return it;
   if (!dx) CUDA_TRY(ctx, cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));

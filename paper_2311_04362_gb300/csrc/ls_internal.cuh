@@ -357,6 +357,9 @@ struct ls_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_done = nullptr;
   cudaEvent_t piece_done[4] = {nullptr, nullptr, nullptr, nullptr};   // host A uploaded piece by piece
+  // ls_solve*: A is put in fixed point on this stream while the QR runs
+  cudaStream_t fx_stream = nullptr;
+  cudaEvent_t fx_done = nullptr;
   // bounded device waits of the fixed-point pass give up after this long
   unsigned long long wait_ns = LS_WAIT_NS;
   // failure injection for tests (ls_inject_fault): the next fixed-point pass's
