@@ -37,13 +37,14 @@
 // results depend on the launch geometry only through the CTA exponents:
 // bit-identical run to run.
 //
-// k_fx_pass is warp-specialized (10 warps, one CTA per SM): a TMA producer
+// k_fx_pass is warp-specialized (18 warps, one CTA per SM): a TMA producer
 // warp streams row tiles of the fixed-point A into a ring of shared stages;
-// warps 0-3 form the exact partial row dots of tile k (four independent
+// warps 0-7 form the exact partial row dots of tile k (four independent
 // accumulator sets per lane, so that the integer multiply-add chains
-// overlap) and hand them over through a two-slot ring; one epilogue warp
-// finishes the rows (r_j, the norms, the fixed point of r_j) and hands them
-// to warps 4-7, which accumulate A^T r for their columns.  The three groups
+// overlap; two warps per sub-partition hide each other's latency) and hand
+// them over through a two-slot ring; one epilogue warp finishes the rows
+// (r_j, the norms, the fixed point of r_j) and hands them to warps 8-15,
+// which accumulate A^T r for their columns.  The three groups
 // work on different tiles at once; every hand-off is an mbarrier and every
 // wait is bounded by the context's wait limit (a group that gives up leaves
 // its loop as a whole warp, so no barrier is left waiting).
@@ -53,8 +54,8 @@ namespace lsk {
 
 namespace {
 
-constexpr int kFxRW = 4;                        // row-group warps
-constexpr int kFxCW = 4;                        // column-group warps
+constexpr int kFxRW = 8;                        // row-group warps (two per sub-partition)
+constexpr int kFxCW = 8;                        // column-group warps
 constexpr int kFxThreads = (kFxRW + kFxCW + 2) * 32;   // + producer + epilogue warp
 constexpr int kFxFoldRows = 64;                 // column sums are folded at most every 64 rows
 constexpr int kNoExp = INT_MIN;                 // "no nonzero value yet"
@@ -115,6 +116,55 @@ __device__ __forceinline__ double i128_to_double(__int128 s) {
   const long long hi = (long long)(s >> 64);
   const unsigned long long lo = (unsigned long long)s;
   return fma((double)hi, 0x1p64, (double)lo);
+}
+
+// Bit length of a nonzero 128-bit magnitude.
+__device__ __forceinline__ int bitlen_u128(unsigned __int128 mag) {
+  const uint64_t hi = (uint64_t)(mag >> 64), lo = (uint64_t)mag;
+  return hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+}
+
+// round(v 2^t) to nearest, ties to even, for a 128-bit v (the caller keeps
+// the result within 2^63).
+__device__ __forceinline__ int64_t round_shift_i128(__int128 v, int t) {
+  if (t >= 0) return (int64_t)(v << t);
+  const int s = -t;
+  if (s >= 127) return 0;
+  const bool neg = v < 0;
+  const unsigned __int128 mag = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  unsigned __int128 q = mag >> s;
+  const unsigned __int128 rem = mag & ((((unsigned __int128)1) << s) - 1);
+  const unsigned __int128 half = ((unsigned __int128)1) << (s - 1);
+  if (rem > half || (rem == half && (q & 1))) q += 1;
+  return neg ? -(int64_t)q : (int64_t)q;
+}
+
+// Nearest FP64 to v 2^k for a 128-bit integer v, rounded once (ties to even),
+// in integer arithmetic; outside the normal range it falls back to ldexp.
+__device__ __forceinline__ double i128_to_double_scaled(__int128 v, int k) {
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  const unsigned __int128 mag = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const int L = bitlen_u128(mag);
+  uint64_t m;
+  int e2 = L - 1 + k;                            // value in [2^e2, 2^(e2+1))
+  if (L <= 53) {
+    m = (uint64_t)mag << (53 - L);
+  } else {
+    const int s = L - 53;
+    m = (uint64_t)(mag >> s);
+    const unsigned __int128 rem = mag & ((((unsigned __int128)1) << s) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (s - 1);
+    if (rem > half || (rem == half && (m & 1))) {
+      m += 1;
+      if (m == (1ull << 53)) { m >>= 1; e2 += 1; }
+    }
+  }
+  const int be = e2 + 1023;
+  if (be >= 1 && be <= 2046)
+    return __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
+  const double d = ldexp((double)m, e2 - 52);   // m is exact in FP64
+  return neg ? -d : d;
 }
 
 __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
@@ -349,7 +399,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
 
   if (warp == kFxRW + kFxCW + 1) {
     // ------------------------------------------------------------ epilogue warp
-    // lane r finishes row r of each tile: the exact row dot (the four warps'
+    // lane r finishes row r of each tile: the exact row dot (the row warps'
     // partials in warp order), r_j = b_j - (A x)_j, the squared norms, and
     // r_j 2^(e_j - 1077) in fixed point at the CTA's running exponent, handed
     // to the column group with the shift its sums need first.
@@ -385,21 +435,47 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
         if (lane == 0) atomicOr(a.status, LS_DEV_TIMEOUT);
         break;
       }
+      // r_j = b_j - S_j 2^sc is formed exactly in 128 bits (b_j put at the
+      // dot's scale; bits of b_j below 2^sc are rounded) and rounded once;
+      // rho_j's fixed point is then taken from the exact R_j.  A b_j too
+      // large for that scale (or non-finite) takes the FP64 route.
       uint64_t rbits = 0;
       int qj = kNoExp;
+      bool exact = false;
+      __int128 Rx = 0;
+      const int sc = ej + xtop - 2154;
       if (lane < rows) {
         __int128 Sj = 0;
 #pragma unroll
         for (int w = 0; w < kFxRW; ++w) Sj += p1[((size_t)slot * kFxRW + w) * tr + lane];
-        const double ax = scale2(i128_to_double(Sj), ej + xtop - 2154);
-        const double rj = bj - ax;
+        const uint64_t bb = (uint64_t)__double_as_longlong(bj);
+        uint64_t Mb;
+        int beb;
+        fx_decode(bb, Mb, beb);
+        const int shb = beb - 1075 - sc;
+        double rj;
+        if (((bb >> 52) & 0x7FF) != 0x7FF && shb <= 72) {
+          __int128 Bj = (shb >= 0) ? ((__int128)Mb << shb) : (__int128)fx_round_shift(Mb, shb);
+          if (bb >> 63) Bj = -Bj;
+          Rx = Bj - Sj;
+          exact = true;
+          rj = i128_to_double_scaled(Rx, sc);
+        } else {
+          rj = bj - scale2(i128_to_double(Sj), sc);
+        }
         rn2 += rj * rj;
         if (a.r_prev) { const double dl = rj - rpj; dn2 += dl * dl; }
         if (a.r_out) a.r_out[row0 + lane] = rj;
         rbits = (uint64_t)__double_as_longlong(rj);
         const int e = (int)((rbits >> 52) & 0x7FF);
-        if (e == 0x7FF) bad = 1;
-        else if (rj != 0.0) qj = (e ? e : 1) + ej;
+        if (e == 0x7FF) {
+          bad = 1;
+          exact = false;
+        } else if (exact) {
+          if (Rx != 0) qj = bitlen_u128(Rx < 0 ? (unsigned __int128)(-Rx) : (unsigned __int128)Rx) + sc + 1022 + ej;
+        } else if (rj != 0.0) {
+          qj = (e ? e : 1) + ej;
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&pfree[slot]);
@@ -408,7 +484,9 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
       Ecta = Enew;
       if (lane < tr) {
         int64_t P = 0;
-        if (qj != kNoExp) {
+        if (qj != kNoExp && exact) {
+          P = round_shift_i128(Rx, sc + ej + 1077 - Ecta);      // |P| < 2^55 since qj <= Ecta
+        } else if (qj != kNoExp) {
           uint64_t M;
           int be;
           fx_decode(rbits, M, be);
@@ -626,7 +704,6 @@ cudaError_t launch_fx_pass(ls_ctx* ctx, const CUtensorMap& map, const FxGeom& g,
   if (npt2 <= 1) return launch_fx_t<1>(ctx, map, g, a);
   if (npt2 <= 2) return launch_fx_t<2>(ctx, map, g, a);
   if (npt2 <= 4) return launch_fx_t<4>(ctx, map, g, a);
-  if (npt2 <= 8) return launch_fx_t<8>(ctx, map, g, a);
   return cudaErrorInvalidValue;
 }
 
