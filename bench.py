@@ -39,6 +39,7 @@ WORKLOAD = ("large single FP64 problem: m=2,000,000, n=1000, kappa=1e8, ||r||=1e
 # HBM copy bandwidth when MEASURED_PEAKS.json is absent (one earlier GB300
 # measurement, the profiling recipe's fallback).
 HBM_FALLBACK_GBS = 6800.0
+EXTRA_ITERS = 3        # updates after the stopping rule first holds, as ls_default_opts sets
 
 # ncu DRAM traffic (read + write bytes) of one fixed-point pass launch on this
 # workload, keyed by the hash of the kernel source it was taken on (a stale
@@ -188,7 +189,7 @@ def _oracle_sample(iters_hint):
     if iters_hint is None:
         if "iters" not in _SAMPLE_CACHE:
             Ps = problems.make_problem(20000, 100, CFG["kappa"], CFG["resnorm"], 2)
-            _, info = oracle.solve(Ps["A"], Ps["b"], 2000, zeta, CFG["q"], 0)
+            _, info = oracle.solve(Ps["A"], Ps["b"], 2000, zeta, CFG["q"], 0, extra=EXTRA_ITERS)
             _SAMPLE_CACHE["iters"] = info["iters"] + 1
         iters = _SAMPLE_CACHE["iters"]
         how = "oracle count on m=20000, n=100"
@@ -510,7 +511,7 @@ def _oracle_small_solve_worker(_):
     c = problems.SMALL
     P = problems.make_problem(c["m"], c["n"], c["kappa"], c["resnorm"], c["seed"])
     t0 = time.perf_counter()
-    oracle.solve(P["A"], P["b"], c["d"], c["zeta"], c["q"], c["seed"])
+    oracle.solve(P["A"], P["b"], c["d"], c["zeta"], c["q"], c["seed"], extra=EXTRA_ITERS)
     return time.perf_counter() - t0
 
 
@@ -547,7 +548,7 @@ def small_case(ctx, stream, args):
     fe = oracle.forward_error(x.cpu().numpy(), P["x"])
     fe_qr = oracle.forward_error(oracle.qr_solve(P["A"], P["b"]), P["x"])
     t0 = time.perf_counter()
-    xo, io = oracle.solve(P["A"], P["b"], d, c["zeta"], c["q"], c["seed"])
+    xo, io = oracle.solve(P["A"], P["b"], d, c["zeta"], c["q"], c["seed"], extra=EXTRA_ITERS)
     t_or = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0))
     with mp.get_context("spawn").Pool(cores, initializer=_one_thread) as pool:
@@ -555,6 +556,8 @@ def small_case(ctx, stream, args):
     return {"workload": "small single FP64 problem: m=4000, n=50, kappa=1e10, ||r||=1e-6, d=20n=1000, zeta=8, "
                         "seed 0, q<=100",
             "value": 1e3 / ms, "unit": UNIT, "ms_per_solve": ms, "iters": info.iters, "fe": fe, "fe_qr": fe_qr,
+            "phase_ms": {"sketch": info.ms_sketch, "factor": info.ms_factor, "iterate": info.ms_iterate},
+            "launches": info.launches,
             "fe_over_qr": fe / fe_qr,
             "oracle": {"value": 1.0 / t_or, "unit": UNIT, "seconds_per_solve": t_or, "cores": 1,
                        "iters": io["iters"], "fe": oracle.forward_error(xo, P["x"]), "kind": "oracle, fully timed"},

@@ -72,13 +72,15 @@ typedef struct {
 typedef struct {
     double gamma;       /* Sec. 3.3 stopping rule, default 1.0 */
     double rho;         /* Sec. 3.3 stopping rule, default 0.04 */
-    int extra_iters;    /* updates to run after the rule first holds, default 0 */
+    int extra_iters;    /* updates to run after the rule first holds, default 3: the
+                           residual is formed exactly, so further updates still lower
+                           the forward error after the rule's first hold */
     int use_stop;       /* 1: apply the stopping rule (default), 0: run exactly q updates */
     double alpha;       /* App. B, Eq. (B.1) step weight; 1.0 = Algorithm 2 */
     double beta;        /* App. B, Eq. (B.1) momentum weight; 0.0 = Algorithm 2 */
 } ls_opts;
 
-/* Default options: gamma 1, rho 0.04, extra 0, stop on, alpha 1, beta 0. */
+/* Default options: gamma 1, rho 0.04, extra 3, stop on, alpha 1, beta 0. */
 LS_API void ls_default_opts(ls_opts* opts);
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t

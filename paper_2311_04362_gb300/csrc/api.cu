@@ -226,7 +226,7 @@ void ls_default_opts(ls_opts* o) {
   if (!o) return;
   o->gamma = 1.0;
   o->rho = 0.04;
-  o->extra_iters = 0;
+  o->extra_iters = 3;
   o->use_stop = 1;
   o->alpha = 1.0;
   o->beta = 0.0;

@@ -5,9 +5,10 @@
 // Why: on GB300 an FP64 FMA issues at about 1.7 per SM clock while a 32x32 ->
 // 64-bit integer multiply-add (IMAD.WIDE) issues at about 60 (measured by
 // rates.cu).  The FP64 pass needs two FMAs per element of A and is bound by
-// that pipe at ~37% of HBM bandwidth.  Four IMAD.WIDE per element and
-// direction fit the integer units many times over, so this pass is bound by
-// the one read of A from HBM.
+// that pipe at ~37% of HBM bandwidth.  Three IMAD.WIDE per element and
+// direction (Karatsuba's split of the 55 x 55-bit product) fit the integer
+// units several times over; what limits the pass is how fast ten warps can
+// issue them, measured at about 2/3 of the one read of A from HBM.
 //
 // Representation (exact, reversible up to the stated rounding):
 //  * A row j is held in 55-bit fixed point relative to its own binade bound:
@@ -18,16 +19,19 @@
 //    magnitude.  a = hi 2^28 + lo with 0 <= lo < 2^28, stored as int2 {lo, hi}.
 //  * x is held the same way with one exponent for the whole vector (per pass).
 //  * The row dot S_j = sum_k a_jk X_k is formed EXACTLY in 128-bit integers
-//    (hi*hi, hi*lo, lo*hi and lo*lo partial products, accumulated in 64-bit
-//    sums that cannot overflow for the bounded column counts per lane), so
-//    (A x)_j = S_j 2^(e_j + e_x - 2154) carries a single rounding when it is
-//    converted to FP64.  r_j = b_j - (A x)_j is formed in FP64.
+//    from three partial products per entry, hi*Xh, (hi + lo)*(Xh + Xl) and
+//    lo*Xl (the cross term hi*Xl + lo*Xh is the middle one minus the outer
+//    two), accumulated in 64-bit sums that cannot overflow for the bounded
+//    column counts per lane.  b_j is put in the same units and r_j = b_j -
+//    (A x)_j is formed exactly too, so r_j carries a single rounding when it
+//    is converted to FP64.
 //  * For c = A^T r, rho_j = r_j 2^(e_j - 1077) is put in 55-bit fixed point
 //    with one exponent E per CTA (the largest seen so far; when a larger one
 //    arrives the CTA's accumulators are shifted right first), and
 //    sum_j a_jk P_j is accumulated exactly per column in 64-bit partial sums
-//    that are folded every <= 64 rows into a 128-bit accumulator in units of
-//    2^28 (the fold drops bits below 2^28 of a value of order 2^110).
+//    (the same three products) that are folded every <= 32 rows into a
+//    128-bit accumulator in units of 2^28 (the fold drops bits below 2^28 of
+//    a value of order 2^110).
 //  * The per-CTA accumulators are summed exactly by k_fx_reduce after
 //    alignment to the largest CTA exponent, and rounded once to FP64.
 // So r and c carry the rounding of A and x to 55 bits, one rounding each,
@@ -37,14 +41,14 @@
 // results depend on the launch geometry only through the CTA exponents:
 // bit-identical run to run.
 //
-// k_fx_pass is warp-specialized (18 warps, one CTA per SM): a TMA producer
+// k_fx_pass is warp-specialized (10 warps, one CTA per SM): a TMA producer
 // warp streams row tiles of the fixed-point A into a ring of shared stages;
-// warps 0-7 form the exact partial row dots of tile k (four independent
+// warps 0-3 form the exact partial row dots of tile k (four independent
 // accumulator sets per lane, so that the integer multiply-add chains
-// overlap; two warps per sub-partition hide each other's latency) and hand
-// them over through a two-slot ring; one epilogue warp finishes the rows
-// (r_j, the norms, the fixed point of r_j) and hands them to warps 8-15,
-// which accumulate A^T r for their columns.  The three groups
+// overlap) and hand them over through a two-slot ring; one epilogue warp
+// finishes the rows (r_j, the norms, the fixed point of r_j) and hands them
+// to warps 4-7, which accumulate A^T r for their columns.  (Eight warps per
+// group measured no faster: 4.47 against 4.24 ms at m = 2e6, n = 1000.)  The three groups
 // work on different tiles at once; every hand-off is an mbarrier and every
 // wait is bounded by the context's wait limit (a group that gives up leaves
 // its loop as a whole warp, so no barrier is left waiting).
@@ -54,10 +58,10 @@ namespace lsk {
 
 namespace {
 
-constexpr int kFxRW = 8;                        // row-group warps (two per sub-partition)
-constexpr int kFxCW = 8;                        // column-group warps
+constexpr int kFxRW = 4;                        // row-group warps
+constexpr int kFxCW = 4;                        // column-group warps
 constexpr int kFxThreads = (kFxRW + kFxCW + 2) * 32;   // + producer + epilogue warp
-constexpr int kFxFoldRows = 64;                 // column sums are folded at most every 64 rows
+constexpr int kFxFoldRows = 32;                 // column sums are folded at most every 32 rows
 constexpr int kNoExp = INT_MIN;                 // "no nonzero value yet"
 
 // |v| = M 2^(be - 1075), M < 2^53, be >= 1 (subnormals: be = 1, no implicit bit).
@@ -249,11 +253,11 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
   const size_t stage_elems = (size_t)tr * nbox * boxw;
   const int pitch = (nbox == 1) ? boxw : 256;       // elements between rows of one box
-  // layout: tiles [S][stage] | p1 [2][kFxRW][tr] i128 | xs [n] | rslot [S][tr] | rshift [S] | barriers
+  // layout: tiles [S][stage] | p1 [2][kFxRW][tr] i128 | xs [n] int4 | rslot [S][tr] | rshift [S] | barriers
   int2* tiles = reinterpret_cast<int2*>(smem_raw);
   __int128* p1 = reinterpret_cast<__int128*>(tiles + S * stage_elems);
-  int2* xs = reinterpret_cast<int2*>(p1 + 2 * kFxRW * tr);
-  int2* rslot = xs + ((n + 1) & ~1);
+  int4* xs = reinterpret_cast<int4*>(p1 + 2 * kFxRW * tr);     // {lo, hi, lo + hi, 0} of x
+  int2* rslot = reinterpret_cast<int2*>(xs + n);
   int* rshift = reinterpret_cast<int*>(rslot + S * tr);
   uint64_t* full = reinterpret_cast<uint64_t*>(rshift + ((S + 1) & ~1));
   uint64_t* empty = full + S;      // stage consumed (column group)
@@ -290,7 +294,10 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
     if (lane == 0) atomicMax(&s_xtop, top);
     __syncthreads();
     const int xt = s_xtop;
-    for (int i = tid; i < n; i += blockDim.x) xs[i] = fx_limbs(fx_of(xb[i], xt));
+    for (int i = tid; i < n; i += blockDim.x) {
+      const int2 l = fx_limbs(fx_of(xb[i], xt));
+      xs[i] = make_int4(l.x, l.y, l.x + l.y, 0);
+    }
     __syncthreads();
   }
   const int xtop = s_xtop;
@@ -342,52 +349,52 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
       const int2* tl = tiles + (size_t)s * stage_elems;
       const int64_t row0 = (int64_t)t * tr;
       const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
-      int64_t T2[4] = {0, 0, 0, 0}, T1[4] = {0, 0, 0, 0}, T0[4] = {0, 0, 0, 0};
+      // Karatsuba: hi*xh, (hi + lo)*(xh + xl) and lo*xl per entry; the cross
+      // term is TK - T2 - T0 (three multiply-adds instead of four)
+      int64_t T2[4] = {0, 0, 0, 0}, TK[4] = {0, 0, 0, 0}, T0[4] = {0, 0, 0, 0};
       if (rl < rows) {
         for (int qb = 0; qb < nbox; ++qb) {
           const int2* bp = tl + (size_t)qb * tr * pitch + rl * pitch;
-          const int2* xp = xs + qb * 256;
+          const int4* xp = xs + qb * 256;
           const int w = (nbox == 1) ? n : min(256, n - qb * 256);
           int c = rho;
           for (; c + 7 * CS < w; c += 8 * CS) {          // eight columns: all loads, then the products
-            int2 av[8], xv[8];
+            int2 av[8];
+            int4 xv[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) { av[u] = bp[c + u * CS]; xv[u] = xp[c + u * CS]; }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               T2[u & 3] = mad_wide(av[u].y, xv[u].y, T2[u & 3]);
-              T1[u & 3] = mad_wide(av[u].y, xv[u].x, T1[u & 3]);
-              T1[u & 3] = mad_wide(av[u].x, xv[u].y, T1[u & 3]);
+              TK[u & 3] = mad_wide(av[u].x + av[u].y, xv[u].z, TK[u & 3]);
               T0[u & 3] = mad_wide(av[u].x, xv[u].x, T0[u & 3]);
             }
           }
           for (; c + 3 * CS < w; c += 4 * CS) {
-            int2 av[4], xv[4];
+            int2 av[4];
+            int4 xv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) { av[u] = bp[c + u * CS]; xv[u] = xp[c + u * CS]; }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               T2[u] = mad_wide(av[u].y, xv[u].y, T2[u]);
-              T1[u] = mad_wide(av[u].y, xv[u].x, T1[u]);
-              T1[u] = mad_wide(av[u].x, xv[u].y, T1[u]);
+              TK[u] = mad_wide(av[u].x + av[u].y, xv[u].z, TK[u]);
               T0[u] = mad_wide(av[u].x, xv[u].x, T0[u]);
             }
           }
           for (; c < w; c += CS) {
             const int2 av = bp[c];
-            const int2 xv = xp[c];
+            const int4 xv = xp[c];
             T2[0] = mad_wide(av.y, xv.y, T2[0]);
-            T1[0] = mad_wide(av.y, xv.x, T1[0]);
-            T1[0] = mad_wide(av.x, xv.y, T1[0]);
+            TK[0] = mad_wide(av.x + av.y, xv.z, TK[0]);
             T0[0] = mad_wide(av.x, xv.x, T0[0]);
           }
         }
       }
-      // the four sets hold disjoint subsets of the lane's <= 64 columns, so
-      // their sums keep the per-lane bounds
-      const int64_t S2 = (T2[0] + T2[1]) + (T2[2] + T2[3]);
-      const int64_t S1 = (T1[0] + T1[1]) + (T1[2] + T1[3]);
-      const int64_t S0 = (T0[0] + T0[1]) + (T0[2] + T0[3]);
+      // each set holds at most 19 of the lane's columns, so |TK| < 19 (1.5 2^28)^2 < 2^62
+      int64_t S2 = 0, S1 = 0, S0 = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { S2 += T2[u]; S1 += TK[u] - T2[u] - T0[u]; S0 += T0[u]; }
       __int128 V = ((__int128)S2 << 56) + ((__int128)S1 << 28) + (__int128)S0;
       for (int o = LPR >> 1; o > 0; o >>= 1) V += shfl_xor_i128(V, o);
       if (q == 0) p1[((size_t)slot * kFxRW + warp) * tr + rl] = V;
@@ -514,7 +521,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
   // -------------------------------------------------------------- column group
   const int tc = tid - kFxRW * 32;
   constexpr int kCT = kFxCW * 32;
-  int64_t T2[NPT2], T1[NPT2], T0[NPT2];
+  int64_t T2[NPT2], TK[NPT2], T0[NPT2];          // Karatsuba sums, as in the row dots
   __int128 W[NPT2];
   // element offset of (row 0, column) in a stage.  Columns past n still read
   // inside the stage (the TMA zero-filled box columns, or the row's last
@@ -523,7 +530,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
   int off[NPT2];
 #pragma unroll
   for (int u = 0; u < NPT2; ++u) {
-    T2[u] = 0; T1[u] = 0; T0[u] = 0; W[u] = 0;
+    T2[u] = 0; TK[u] = 0; T0[u] = 0; W[u] = 0;
     const int c = tc + kCT * u;
     off[u] = (nbox == 1) ? min(c, boxw - 1) : ((c >> 8) * (tr * 256) + (c & 255));
   }
@@ -531,8 +538,8 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
   auto fold = [&]() {
 #pragma unroll
     for (int u = 0; u < NPT2; ++u) {
-      W[u] += ((__int128)T2[u] << 28) + (__int128)T1[u] + (__int128)(T0[u] >> 28);
-      T2[u] = 0; T1[u] = 0; T0[u] = 0;
+      W[u] += ((__int128)T2[u] << 28) + (__int128)(TK[u] - T2[u] - T0[u]) + (__int128)(T0[u] >> 28);
+      T2[u] = 0; TK[u] = 0; T0[u] = 0;
     }
   };
   int k = 0;
@@ -557,6 +564,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
     }
     for (int r = 0; r < rows; ++r) {
       const int2 pv = rs[r];
+      const int ps = pv.x + pv.y;
       const int2* rowp = tl + r * pitch;
       int2 av[NPT2];
 #pragma unroll
@@ -564,8 +572,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
 #pragma unroll
       for (int u = 0; u < NPT2; ++u) {
         T2[u] = mad_wide(av[u].y, pv.y, T2[u]);
-        T1[u] = mad_wide(av[u].y, pv.x, T1[u]);
-        T1[u] = mad_wide(av[u].x, pv.y, T1[u]);
+        TK[u] = mad_wide(av[u].x + av[u].y, ps, TK[u]);
         T0[u] = mad_wide(av[u].x, pv.x, T0[u]);
       }
     }
@@ -641,7 +648,7 @@ FxGeom fx_geometry(const ls_ctx* ctx, int64_t n, int64_t m) {
   g.stages = (int)std::max<size_t>(2, std::min<size_t>(4, (192 * 1024) / stage));
   const int64_t ntiles = (m + g.tr - 1) / g.tr;
   g.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ntiles));
-  g.smem = g.stages * stage + (size_t)2 * kFxRW * g.tr * 16 + (size_t)((n + 1) & ~1LL) * 8 +
+  g.smem = g.stages * stage + (size_t)2 * kFxRW * g.tr * 16 + (size_t)n * 16 +
            (size_t)g.stages * g.tr * 8 + (size_t)((g.stages + 1) & ~1) * 4 + (4 * (size_t)g.stages + 4) * 8 + 128;
   return g;
 }
@@ -704,6 +711,7 @@ cudaError_t launch_fx_pass(ls_ctx* ctx, const CUtensorMap& map, const FxGeom& g,
   if (npt2 <= 1) return launch_fx_t<1>(ctx, map, g, a);
   if (npt2 <= 2) return launch_fx_t<2>(ctx, map, g, a);
   if (npt2 <= 4) return launch_fx_t<4>(ctx, map, g, a);
+  if (npt2 <= 8) return launch_fx_t<8>(ctx, map, g, a);
   return cudaErrorInvalidValue;
 }
 

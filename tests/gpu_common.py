@@ -3,6 +3,8 @@ tensors from numpy, and the tolerances derived from the rounding analysis."""
 import numpy as np
 
 U = 2.0 ** -53
+# updates the library runs after the stopping rule first holds (ls_default_opts)
+DEFAULT_EXTRA = 3
 
 
 def gamma(k):

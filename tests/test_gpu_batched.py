@@ -27,7 +27,7 @@ import pytest
 
 import oracle
 import problems
-from gpu_common import U, dev, host, padded_rowmajor, require_gpu
+from gpu_common import DEFAULT_EXTRA, U, dev, host, padded_rowmajor, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -123,7 +123,7 @@ def test_batched_solutions_meet_acceptance(env, small_batch):
         k, res = P["kappa"], P["resnorm"]
         wedin = 10 * U * k * (1 + k * res / (np.linalg.norm(P["A"], 2) * np.linalg.norm(P["x"])))
         assert fe <= max(10 * fe_qr, wedin), (s, fe, fe_qr, wedin)
-        xo, io = oracle.solve(P["A"], P["b"], s["d"], 8, 100, s["index"])
+        xo, io = oracle.solve(P["A"], P["b"], s["d"], 8, 100, s["index"], extra=DEFAULT_EXTRA)
         assert oracle.forward_error(xo, P["x"]) <= max(10 * fe_qr, wedin)
         if io["converged"]:
             assert abs(inf.iters - io["iters"]) <= max(5, io["iters"] / 4), (s, inf.iters, io["iters"])

@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 import problems
-from gpu_common import U, dev, gamma, host, padded_rowmajor, require_gpu
+from gpu_common import DEFAULT_EXTRA, U, dev, gamma, host, padded_rowmajor, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -165,7 +165,7 @@ def test_solve_small_config_forward_error(env, kappa, res):
     st, info = ctx.ls_solve(dev(torch, P["A"]), dev(torch, P["b"]), 4000, 50, 50, 1000, 8, 100, 0, x)
     fe = oracle.forward_error(host(x), P["x"])
     fe_qr = oracle.forward_error(oracle.qr_solve(P["A"], P["b"]), P["x"])
-    xo, io = oracle.solve(P["A"], P["b"], 1000, 8, 100, 0)
+    xo, io = oracle.solve(P["A"], P["b"], 1000, 8, 100, 0, extra=DEFAULT_EXTRA)
     assert st == ls.LS_OK and info.stop_reason == 0
     assert fe <= 10 * fe_qr, (fe, fe_qr)
     assert abs(info.iters - io["iters"]) <= 5

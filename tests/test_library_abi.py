@@ -42,7 +42,7 @@ def test_library_loads_and_binds(libpath):
     for s in declared_symbols():
         assert hasattr(L, s)
     o = ls.default_opts()
-    assert (o.gamma, o.rho, o.extra_iters, o.use_stop, o.alpha, o.beta) == (1.0, 0.04, 0, 1, 1.0, 0.0)
+    assert (o.gamma, o.rho, o.extra_iters, o.use_stop, o.alpha, o.beta) == (1.0, 0.04, 3, 1, 1.0, 0.0)
     # no GPU here: creating a context must fail with a status, not crash
     h = ctypes.c_void_p()
     st = L.ls_create(ctypes.byref(h), 0, None)
