@@ -64,6 +64,14 @@ constexpr int kFxThreads = (kFxRW + kFxCW + 2) * 32;   // + producer + epilogue 
 constexpr int kFxFoldRows = 32;                 // column sums are folded at most every 32 rows
 constexpr int kNoExp = INT_MIN;                 // "no nonzero value yet"
 
+// Rows per tile of the instantiation NPT2 (1, 2, 4, 6, 8; it serves the n
+// with ceil(n / 128) <= NPT2): 32 for n <= 256 (one box per row), 16 for
+// n <= 512 (two boxes of 256 columns), 8 for n <= 1024 (three or four).
+// fx_geometry picks the same; a compile-time value turns the shared-memory
+// offsets of the inner loops into immediates.  NPT2 128 <= 256 nbox, so the
+// column lanes' loads stay inside the stage's boxes.
+__host__ __device__ constexpr int fx_tile_rows(int npt2) { return npt2 >= 5 ? 8 : (npt2 >= 3 ? 16 : 32); }
+
 // |v| = M 2^(be - 1075), M < 2^53, be >= 1 (subnormals: be = 1, no implicit bit).
 __device__ __forceinline__ void fx_decode(uint64_t bits, uint64_t& M, int& be) {
   const int e = (int)((bits >> 52) & 0x7FF);
@@ -184,16 +192,21 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
 // phase completes (or the hint runs out) instead of spinning: spinning
 // waiters took issue slots and shared-memory bandwidth from the warps doing
 // the work on the same sub-partition.  False once `ns` have passed.
+__device__ __forceinline__ bool fx_try(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 __device__ __forceinline__ bool fx_wait(uint64_t* bar, uint32_t parity, unsigned long long ns) {
+  if (fx_try(bar, parity, 20000u)) return true;   // the clock is read only when the phase is not complete yet
   const uint64_t deadline = gtimer() + ns;
   for (;;) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
-        : "memory");
-    if (ok) return true;
+    if (fx_try(bar, parity, 20000u)) return true;
     if (gtimer() > deadline) return false;
   }
 }
@@ -249,15 +262,18 @@ template <int NPT2>
 __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant__ CUtensorMap map, FxArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (a.st && a.st->done) return;
-  const int n = a.n, tr = a.tr, boxw = a.boxw, nbox = a.nbox, S = a.stages;
+  constexpr int tr = fx_tile_rows(NPT2);
+  constexpr bool kBoxed = NPT2 >= 4;                // rows cut into boxes of 256 columns (n > 256)
+  const int n = a.n, boxw = kBoxed ? 256 : a.boxw, nbox = a.nbox, S = a.stages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
   const size_t stage_elems = (size_t)tr * nbox * boxw;
-  const int pitch = (nbox == 1) ? boxw : 256;       // elements between rows of one box
+  const int pitch = kBoxed ? 256 : boxw;            // elements between rows of one box
   // layout: tiles [S][stage] | p1 [2][kFxRW][tr] i128 | xs [n] int4 | rslot [S][tr] | rshift [S] | barriers
   int2* tiles = reinterpret_cast<int2*>(smem_raw);
   __int128* p1 = reinterpret_cast<__int128*>(tiles + S * stage_elems);
   int4* xs = reinterpret_cast<int4*>(p1 + 2 * kFxRW * tr);     // {lo, hi, lo + hi, 0} of x
-  int2* rslot = reinterpret_cast<int2*>(xs + n);
+  const int xlen = kBoxed ? nbox * 256 : n;          // boxed rows: zero-padded to whole boxes
+  int2* rslot = reinterpret_cast<int2*>(xs + xlen);
   int* rshift = reinterpret_cast<int*>(rslot + S * tr);
   uint64_t* full = reinterpret_cast<uint64_t*>(rshift + ((S + 1) & ~1));
   uint64_t* empty = full + S;      // stage consumed (column group)
@@ -294,8 +310,8 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
     if (lane == 0) atomicMax(&s_xtop, top);
     __syncthreads();
     const int xt = s_xtop;
-    for (int i = tid; i < n; i += blockDim.x) {
-      const int2 l = fx_limbs(fx_of(xb[i], xt));
+    for (int i = tid; i < xlen; i += blockDim.x) {
+      const int2 l = (i < n) ? fx_limbs(fx_of(xb[i], xt)) : make_int2(0, 0);
       xs[i] = make_int4(l.x, l.y, l.x + l.y, 0);
     }
     __syncthreads();
@@ -330,11 +346,13 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
 
   if (warp < kFxRW) {
     // ------------------------------------------------------------ row warps
-    // lane (rl, q) of warp w sums row rl over the columns rho + i CS of each
-    // box (rotated by rl so that the rows of a warp sit on different banks),
-    // in four independent accumulator sets; the lanes of a row are combined
-    // by shuffles and each warp's row partials go to the epilogue warp.
-    const int LPR = 32 / tr, CS = kFxRW * LPR;
+    // lane (rl, q) of warp w sums rows rl + g RG (g < RPL) over the columns
+    // rho + i CS of each box (rotated by rl so that the rows of a warp sit on
+    // different banks), in four independent accumulator sets per row; each x
+    // value loaded serves RPL rows.  The lanes of a row are combined by
+    // shuffles and each warp's row partials go to the epilogue warp.  Rows
+    // past m read the TMA's zero fill, so every lane runs the same loop.
+    constexpr int RPL = 2, LPR = 32 * RPL / tr, CS = kFxRW * LPR, RG = tr / RPL;
     const int rl = lane / LPR, q = lane - rl * LPR;
     const int rho = LPR * ((warp + rl) % kFxRW) + q;
     int k = 0;
@@ -347,57 +365,88 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
         break;
       }
       const int2* tl = tiles + (size_t)s * stage_elems;
-      const int64_t row0 = (int64_t)t * tr;
-      const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
       // Karatsuba: hi*xh, (hi + lo)*(xh + xl) and lo*xl per entry; the cross
       // term is TK - T2 - T0 (three multiply-adds instead of four)
-      int64_t T2[4] = {0, 0, 0, 0}, TK[4] = {0, 0, 0, 0}, T0[4] = {0, 0, 0, 0};
-      if (rl < rows) {
+      int64_t T2[RPL][4], TK[RPL][4], T0[RPL][4];
+#pragma unroll
+      for (int g = 0; g < RPL; ++g)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { T2[g][u] = 0; TK[g][u] = 0; T0[g][u] = 0; }
+      if (kBoxed) {
+        // every box is walked at its full 256 columns: columns past n hold
+        // the TMA's zero fill and x is zero-padded there, so all lanes run
+        // the same compile-time loop (NB blocks of eight columns per box)
+        constexpr int NB = 256 / (8 * CS);
         for (int qb = 0; qb < nbox; ++qb) {
-          const int2* bp = tl + (size_t)qb * tr * pitch + rl * pitch;
-          const int4* xp = xs + qb * 256;
-          const int w = (nbox == 1) ? n : min(256, n - qb * 256);
-          int c = rho;
-          for (; c + 7 * CS < w; c += 8 * CS) {          // eight columns: all loads, then the products
-            int2 av[8];
+          const int2* bp = tl + (size_t)qb * tr * 256 + rl * 256 + rho;
+          const int4* xp = xs + qb * 256 + rho;
+#pragma unroll
+          for (int blk = 0; blk < NB; ++blk) {
+            int2 av[RPL][8];
             int4 xv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) { av[u] = bp[c + u * CS]; xv[u] = xp[c + u * CS]; }
-#pragma unroll
             for (int u = 0; u < 8; ++u) {
-              T2[u & 3] = mad_wide(av[u].y, xv[u].y, T2[u & 3]);
-              TK[u & 3] = mad_wide(av[u].x + av[u].y, xv[u].z, TK[u & 3]);
-              T0[u & 3] = mad_wide(av[u].x, xv[u].x, T0[u & 3]);
-            }
-          }
-          for (; c + 3 * CS < w; c += 4 * CS) {
-            int2 av[4];
-            int4 xv[4];
+              xv[u] = xp[(blk * 8 + u) * CS];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) { av[u] = bp[c + u * CS]; xv[u] = xp[c + u * CS]; }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              T2[u] = mad_wide(av[u].y, xv[u].y, T2[u]);
-              TK[u] = mad_wide(av[u].x + av[u].y, xv[u].z, TK[u]);
-              T0[u] = mad_wide(av[u].x, xv[u].x, T0[u]);
+              for (int g = 0; g < RPL; ++g) av[g][u] = bp[g * RG * 256 + (blk * 8 + u) * CS];
             }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+              for (int g = 0; g < RPL; ++g) {
+                T2[g][u & 3] = mad_wide(av[g][u].y, xv[u].y, T2[g][u & 3]);
+                TK[g][u & 3] = mad_wide(av[g][u].x + av[g][u].y, xv[u].z, TK[g][u & 3]);
+                T0[g][u & 3] = mad_wide(av[g][u].x, xv[u].x, T0[g][u & 3]);
+              }
           }
-          for (; c < w; c += CS) {
-            const int2 av = bp[c];
-            const int4 xv = xp[c];
-            T2[0] = mad_wide(av.y, xv.y, T2[0]);
-            TK[0] = mad_wide(av.x + av.y, xv.z, TK[0]);
-            T0[0] = mad_wide(av.x, xv.x, T0[0]);
+        }
+      } else {
+        const int2* bp = tl + rl * pitch;
+        const int4* xp = xs;
+        const int w = n;
+        int c = rho;
+        for (; c + 7 * CS < w; c += 8 * CS) {          // eight columns: all loads, then the products
+          int2 av[RPL][8];
+          int4 xv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            xv[u] = xp[c + u * CS];
+#pragma unroll
+            for (int g = 0; g < RPL; ++g) av[g][u] = bp[g * RG * pitch + c + u * CS];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int g = 0; g < RPL; ++g) {
+              T2[g][u & 3] = mad_wide(av[g][u].y, xv[u].y, T2[g][u & 3]);
+              TK[g][u & 3] = mad_wide(av[g][u].x + av[g][u].y, xv[u].z, TK[g][u & 3]);
+              T0[g][u & 3] = mad_wide(av[g][u].x, xv[u].x, T0[g][u & 3]);
+            }
+        }
+        for (; c < w; c += CS) {
+          const int4 xv = xp[c];
+#pragma unroll
+          for (int g = 0; g < RPL; ++g) {
+            const int2 av = bp[g * RG * pitch + c];
+            T2[g][0] = mad_wide(av.y, xv.y, T2[g][0]);
+            TK[g][0] = mad_wide(av.x + av.y, xv.z, TK[g][0]);
+            T0[g][0] = mad_wide(av.x, xv.x, T0[g][0]);
           }
         }
       }
-      // each set holds at most 19 of the lane's columns, so |TK| < 19 (1.5 2^28)^2 < 2^62
-      int64_t S2 = 0, S1 = 0, S0 = 0;
+      // a set holds at most 13 of the lane's columns (8 for boxed rows; with
+      // one box, n / 32 <= 8 plus a tail of up to 7 in set 0), so
+      // |TK| < 13 (1.5 2^28)^2 < 2^62
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { S2 += T2[u]; S1 += TK[u] - T2[u] - T0[u]; S0 += T0[u]; }
-      __int128 V = ((__int128)S2 << 56) + ((__int128)S1 << 28) + (__int128)S0;
-      for (int o = LPR >> 1; o > 0; o >>= 1) V += shfl_xor_i128(V, o);
-      if (q == 0) p1[((size_t)slot * kFxRW + warp) * tr + rl] = V;
+      for (int g = 0; g < RPL; ++g) {
+        int64_t S2 = 0, S1 = 0, S0 = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { S2 += T2[g][u]; S1 += TK[g][u] - T2[g][u] - T0[g][u]; S0 += T0[g][u]; }
+        __int128 V = ((__int128)S2 << 56) + ((__int128)S1 << 28) + (__int128)S0;
+#pragma unroll
+        for (int o = LPR >> 1; o > 0; o >>= 1) V += shfl_xor_i128(V, o);
+        if (q == 0) p1[((size_t)slot * kFxRW + warp) * tr + rl + g * RG] = V;
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&pready[slot]);
     }
@@ -532,7 +581,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
   for (int u = 0; u < NPT2; ++u) {
     T2[u] = 0; TK[u] = 0; T0[u] = 0; W[u] = 0;
     const int c = tc + kCT * u;
-    off[u] = (nbox == 1) ? min(c, boxw - 1) : ((c >> 8) * (tr * 256) + (c & 255));
+    off[u] = kBoxed ? 0 : min(c, boxw - 1);         // boxed rows: compile-time offsets below
   }
   int since = 0;
   auto fold = [&]() {
@@ -562,19 +611,27 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
 #pragma unroll
       for (int u = 0; u < NPT2; ++u) W[u] = (sh >= 120) ? (__int128)0 : (W[u] >> sh);
     }
-    for (int r = 0; r < rows; ++r) {
+    // column tc + 128 u of a boxed row sits in box u / 2 at tc + 128 (u % 2)
+    const int2* cb = tl + (kBoxed ? tc : 0);
+    auto col_row = [&](int r) {
       const int2 pv = rs[r];
       const int ps = pv.x + pv.y;
-      const int2* rowp = tl + r * pitch;
       int2 av[NPT2];
 #pragma unroll
-      for (int u = 0; u < NPT2; ++u) av[u] = rowp[off[u]];     // all loads first
+      for (int u = 0; u < NPT2; ++u)                  // all loads first
+        av[u] = kBoxed ? cb[r * 256 + (u >> 1) * (tr * 256) + 128 * (u & 1)] : tl[r * pitch + off[u]];
 #pragma unroll
       for (int u = 0; u < NPT2; ++u) {
         T2[u] = mad_wide(av[u].y, pv.y, T2[u]);
         TK[u] = mad_wide(av[u].x + av[u].y, ps, TK[u]);
         T0[u] = mad_wide(av[u].x, pv.x, T0[u]);
       }
+    };
+    if (rows == tr) {
+#pragma unroll
+      for (int r = 0; r < tr; ++r) col_row(r);
+    } else {
+      for (int r = 0; r < rows; ++r) col_row(r);
     }
     since += rows;
     if (since + tr > kFxFoldRows) { fold(); since = 0; }
@@ -648,7 +705,8 @@ FxGeom fx_geometry(const ls_ctx* ctx, int64_t n, int64_t m) {
   g.stages = (int)std::max<size_t>(2, std::min<size_t>(4, (192 * 1024) / stage));
   const int64_t ntiles = (m + g.tr - 1) / g.tr;
   g.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ntiles));
-  g.smem = g.stages * stage + (size_t)2 * kFxRW * g.tr * 16 + (size_t)n * 16 +
+  const size_t xlen = (g.nbox > 1) ? (size_t)g.nbox * 256 : (size_t)n;
+  g.smem = g.stages * stage + (size_t)2 * kFxRW * g.tr * 16 + xlen * 16 +
            (size_t)g.stages * g.tr * 8 + (size_t)((g.stages + 1) & ~1) * 4 + (4 * (size_t)g.stages + 4) * 8 + 128;
   return g;
 }
@@ -689,6 +747,9 @@ cudaError_t make_fx_tensor_map(ls_ctx* ctx, CUtensorMap* map, const int2* Af, in
 
 template <int NPT2>
 static cudaError_t launch_fx_t(ls_ctx* ctx, const CUtensorMap& map, const FxGeom& g, const FxArgs& a) {
+  if (g.tr != fx_tile_rows(NPT2) || (g.nbox > 1) != (NPT2 >= 4) ||
+      (g.nbox > 1 && (g.boxw != 256 || NPT2 * 128 > g.nbox * 256)))
+    return cudaErrorInvalidValue;                   // the kernel's compile-time tile shape
   cudaError_t e = cudaFuncSetAttribute(k_fx_pass<NPT2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
   if (e != cudaSuccess) return e;
   k_fx_pass<NPT2><<<g.grid, kFxThreads, g.smem, ctx->stream>>>(map, a);
@@ -711,6 +772,7 @@ cudaError_t launch_fx_pass(ls_ctx* ctx, const CUtensorMap& map, const FxGeom& g,
   if (npt2 <= 1) return launch_fx_t<1>(ctx, map, g, a);
   if (npt2 <= 2) return launch_fx_t<2>(ctx, map, g, a);
   if (npt2 <= 4) return launch_fx_t<4>(ctx, map, g, a);
+  if (npt2 <= 6) return launch_fx_t<6>(ctx, map, g, a);
   if (npt2 <= 8) return launch_fx_t<8>(ctx, map, g, a);
   return cudaErrorInvalidValue;
 }

@@ -83,8 +83,10 @@ def test_fixed_point_form_is_its_definition(env):
 PASS_CASES = [(4000, 50), (1, 1), (7, 3), (1000, 17), (999, 31), (1003, 32), (1001, 33), (2049, 64),
               (3000, 100), (300, 255), (300, 256), (5001, 257), (4000, 300), (2000, 512), (2000, 513),
               (3007, 1000), (2100, 1024),
-              # many tiles per CTA: rings wrap, sums cross tiles and fold points
-              (200_000, 50), (200_000, 200), (200_001, 1000)]
+              # many tiles per CTA: rings wrap (every stage in use), sums cross
+              # tiles and fold points; three boxes of 256 columns (n in (512, 768])
+              # and a ragged last box
+              (200_000, 50), (200_000, 200), (150_001, 300), (200_000, 520), (200_003, 700), (200_001, 1000)]
 
 
 @pytest.mark.parametrize("m,n", PASS_CASES)
