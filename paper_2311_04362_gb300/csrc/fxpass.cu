@@ -41,17 +41,21 @@
 // results depend on the launch geometry only through the CTA exponents:
 // bit-identical run to run.
 //
-// k_fx_pass is warp-specialized (10 warps, one CTA per SM): a TMA producer
+// k_fx_pass is warp-specialized (11 warps, one CTA per SM): a TMA producer
 // warp streams row tiles of the fixed-point A into a ring of shared stages;
-// warps 0-3 form the exact partial row dots of tile k (four independent
-// accumulator sets per lane, so that the integer multiply-add chains
-// overlap) and hand them over through a two-slot ring; one epilogue warp
-// finishes the rows (r_j, the norms, the fixed point of r_j) and hands them
-// to warps 4-7, which accumulate A^T r for their columns.  (Eight warps per
-// group measured no faster: 4.47 against 4.24 ms at m = 2e6, n = 1000.)  The three groups
-// work on different tiles at once; every hand-off is an mbarrier and every
-// wait is bounded by the context's wait limit (a group that gives up leaves
-// its loop as a whole warp, so no barrier is left waiting).
+// warps 0-3 form the exact partial row dots of tile k (each lane two rows of
+// the tile, in four independent accumulator sets per row, so that the
+// integer multiply-add chains overlap) and hand them over through a two-slot
+// ring; two epilogue warps, taking alternate tiles, finish the rows (r_j, the
+// norms, the fixed point of r_j at the CTA's running exponent, which passes
+// from one to the other) and hand them to warps 4-7, which accumulate A^T r
+// for their columns.  The groups work on different tiles at once; every
+// hand-off is an mbarrier and every wait is bounded by the context's wait
+// limit (a group that gives up leaves its loop as a whole warp, so no
+// barrier is left waiting).  Measured at m = 2e6, n = 1000 on the way:
+// eight row and eight column warps, 4.47 ms against 4.24 with four each;
+// one barrier per 256-column box instead of per tile (the row warps start on
+// a tile's first box), 3.69 against 3.22 ms.
 #include "ls_internal.cuh"
 
 namespace lsk {
@@ -60,7 +64,8 @@ namespace {
 
 constexpr int kFxRW = 4;                        // row-group warps
 constexpr int kFxCW = 4;                        // column-group warps
-constexpr int kFxThreads = (kFxRW + kFxCW + 2) * 32;   // + producer + epilogue warp
+constexpr int kFxEW = 2;                        // epilogue warps (alternate tiles)
+constexpr int kFxThreads = (kFxRW + kFxCW + 1 + kFxEW) * 32;   // + producer
 constexpr int kFxFoldRows = 32;                 // column sums are folded at most every 32 rows
 constexpr int kNoExp = INT_MIN;                 // "no nonzero value yet"
 
@@ -282,6 +287,13 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
   uint64_t* pready = rfree + S;    // [2] row-dot partials of a tile written (row warps)
   uint64_t* pfree = pready + 2;    // [2] row-dot partials read (epilogue warp)
   __shared__ int s_xtop, s_xbad;
+  // the running CTA exponent handed from the epilogue warp of tile k to that
+  // of tile k + 1 (value and barrier per parity of k), and the second
+  // epilogue warp's sums for the partial written at the end
+  __shared__ __align__(8) uint64_t s_eready[2];
+  __shared__ int s_ecta[2];
+  __shared__ double s_esum[2];
+  __shared__ int s_eflag[2];
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -290,7 +302,11 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
       mbar_init(&rready[s], 1);
       mbar_init(&rfree[s], kFxCW);
     }
-    for (int i = 0; i < 2; ++i) { mbar_init(&pready[i], kFxRW); mbar_init(&pfree[i], 1); }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&pready[i], kFxRW);
+      mbar_init(&pfree[i], 1);
+      mbar_init(&s_eready[i], 1);
+    }
     fence_mbar_init();
     s_xtop = 1;
     s_xbad = 0;
@@ -453,16 +469,21 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
     return;
   }
 
-  if (warp == kFxRW + kFxCW + 1) {
-    // ------------------------------------------------------------ epilogue warp
-    // lane r finishes row r of each tile: the exact row dot (the row warps'
-    // partials in warp order), r_j = b_j - (A x)_j, the squared norms, and
-    // r_j 2^(e_j - 1077) in fixed point at the CTA's running exponent, handed
-    // to the column group with the shift its sums need first.
+  if (warp > kFxRW + kFxCW) {
+    // ------------------------------------------------------------ epilogue warps
+    // Epilogue warp e takes the tiles k = e, e + 2, ... of the CTA (its slot
+    // of the row-dot ring is e).  Lane r finishes row r of a tile: the exact
+    // row dot (the row warps' partials in warp order), r_j = b_j - (A x)_j,
+    // the squared norms, and r_j 2^(e_j - 1077) in fixed point at the CTA's
+    // running exponent, handed to the column group with the shift its sums
+    // need first.  The running exponent is the one sequential step: tile k
+    // takes tile k - 1's from the other warp (s_ecta / s_eready) after its
+    // own rows are done, so the two warps' row work overlaps.
+    const int e = warp - (kFxRW + kFxCW + 1);
     double rn2 = 0.0, dn2 = 0.0;
     int Ecta = kNoExp, bad = 0;
-    // the row scalars (b, e_j, r_prev) of the next tile are loaded one tile
-    // ahead, so their global-memory latency is not on the hand-off path
+    // the row scalars (b, e_j, r_prev) of the warp's next tile are loaded one
+    // tile ahead, so their global-memory latency is not on the hand-off path
     double nb = 0.0, nrp = 0.0;
     int ne = 0;
     auto load_next = [&](int tn) {
@@ -476,15 +497,16 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
         }
       }
     };
-    load_next(blockIdx.x);
-    int k = 0;
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++k) {
+    const int stride = kFxEW * gridDim.x;
+    load_next(blockIdx.x + e * gridDim.x);
+    int k = e;
+    for (int t = blockIdx.x + e * gridDim.x; t < a.ntiles; t += stride, k += kFxEW) {
       const int s = k % S, slot = k & 1;
       const int64_t row0 = (int64_t)t * tr;
       const int rows = (int)((a.m - row0 < (int64_t)tr) ? (a.m - row0) : (int64_t)tr);
       const double bj = nb, rpj = nrp;
       const int ej = ne;
-      load_next(t + gridDim.x);
+      load_next(t + stride);
       bool ok = fx_wait(&pready[slot], (k >> 1) & 1, a.wait_ns);
       if (ok && k >= S) ok = fx_wait(&rfree[s], ((k / S) - 1) & 1, a.wait_ns);
       if (!__all_sync(0xffffffffu, ok)) {
@@ -523,21 +545,38 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
         if (a.r_prev) { const double dl = rj - rpj; dn2 += dl * dl; }
         if (a.r_out) a.r_out[row0 + lane] = rj;
         rbits = (uint64_t)__double_as_longlong(rj);
-        const int e = (int)((rbits >> 52) & 0x7FF);
-        if (e == 0x7FF) {
+        const int ex = (int)((rbits >> 52) & 0x7FF);
+        if (ex == 0x7FF) {
           bad = 1;
           exact = false;
         } else if (exact) {
           if (Rx != 0) qj = bitlen_u128(Rx < 0 ? (unsigned __int128)(-Rx) : (unsigned __int128)Rx) + sc + 1022 + ej;
         } else if (rj != 0.0) {
-          qj = (e ? e : 1) + ej;
+          qj = (ex ? ex : 1) + ej;
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&pfree[slot]);
-      const int Enew = max(Ecta, warp_max_int(qj));
-      const int shift = (Ecta == kNoExp || Enew == kNoExp) ? 0 : Enew - Ecta;
+      const int qmax = warp_max_int(qj);
+      // the running exponent after tile k - 1 (the other warp's)
+      int Eprev = kNoExp;
+      if (k >= 1) {
+        const int kp = k - 1;
+        ok = fx_wait(&s_eready[kp & 1], (kp >> 1) & 1, a.wait_ns);
+        if (!__all_sync(0xffffffffu, ok)) {
+          if (lane == 0) atomicOr(a.status, LS_DEV_TIMEOUT);
+          break;
+        }
+        Eprev = s_ecta[kp & 1];
+      }
+      const int Enew = max(Eprev, qmax);
+      const int shift = (Eprev == kNoExp || Enew == kNoExp) ? 0 : Enew - Eprev;
       Ecta = Enew;
+      __syncwarp();
+      if (lane == 0) {
+        s_ecta[k & 1] = Enew;          // tile k + 1 read s_ecta[(k - 1) & 1] before
+        mbar_arrive(&s_eready[k & 1]);   // this warp could pass its own wait
+      }
       if (lane < tr) {
         int64_t P = 0;
         if (qj != kNoExp && exact) {
@@ -558,11 +597,20 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
     rn2 = warp_sum(rn2);
     dn2 = warp_sum(dn2);
     bad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) {
-      out[2 * n] = (long long)Ecta;
-      out[2 * n + 1] = __double_as_longlong(rn2);
-      out[2 * n + 2] = __double_as_longlong(dn2);
-      out[2 * n + 3] = s_xbad | (bad ? 2 : 0);
+    // warp 1 hands its sums to warp 0, which writes the CTA's partial (the
+    // two epilogue warps meet at named barrier 1; both leave their loops)
+    if (e == 1 && lane == 0) {
+      s_esum[0] = rn2;
+      s_esum[1] = dn2;
+      s_eflag[0] = bad;
+      s_eflag[1] = Ecta;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(kFxEW * 32) : "memory");
+    if (e == 0 && lane == 0) {
+      out[2 * n] = (long long)max(Ecta, s_eflag[1]);
+      out[2 * n + 1] = __double_as_longlong(rn2 + s_esum[0]);
+      out[2 * n + 2] = __double_as_longlong(dn2 + s_esum[1]);
+      out[2 * n + 3] = s_xbad | ((bad | s_eflag[0]) ? 2 : 0);
     }
     return;
   }
