@@ -141,47 +141,32 @@ __device__ __forceinline__ int bitlen_u128(unsigned __int128 mag) {
   return hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
 }
 
-// round(v 2^t) to nearest, ties to even, for a 128-bit v (the caller keeps
-// the result within 2^63).
-__device__ __forceinline__ int64_t round_shift_i128(__int128 v, int t) {
-  if (t >= 0) return (int64_t)(v << t);
-  const int s = -t;
-  if (s >= 127) return 0;
-  const bool neg = v < 0;
-  const unsigned __int128 mag = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-  unsigned __int128 q = mag >> s;
-  const unsigned __int128 rem = mag & ((((unsigned __int128)1) << s) - 1);
-  const unsigned __int128 half = ((unsigned __int128)1) << (s - 1);
-  if (rem > half || (rem == half && (q & 1))) q += 1;
-  return neg ? -(int64_t)q : (int64_t)q;
+// The rounding of a normalised magnitude: |v| = N 2^(e - 127) with N the
+// 128-bit value whose top 64 bits are Nh (bit 63 set) and whose lower bits
+// are nonzero iff Ns.  fx_round53 gives the FP64 nearest to +-|v| when
+// |v| is in [2^e, 2^(e+1)) (ties to even; outside the normal range ldexp);
+// fx_round_norm gives round(|v| 2^(w - e - 1)) for the integer whose bit
+// length is w <= 63 (the value N 2^(w - 128)), ties to even.
+__device__ __forceinline__ double fx_round53(uint64_t Nh, bool Ns, bool neg, int e) {
+  uint64_t q = Nh >> 11;
+  const uint64_t rem = Nh & 0x7FFull;
+  q += (rem > 0x400ull) || (rem == 0x400ull && (Ns || (q & 1ull)));
+  if (q >> 53) { q >>= 1; e += 1; }
+  const int be = e + 1023;
+  if (be >= 1 && be <= 2046)
+    return __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)be << 52) | (q & 0xFFFFFFFFFFFFFull)));
+  const double d = ldexp((double)q, e - 52);   // q is exact in FP64
+  return neg ? -d : d;
 }
 
-// Nearest FP64 to v 2^k for a 128-bit integer v, rounded once (ties to even),
-// in integer arithmetic; outside the normal range it falls back to ldexp.
-__device__ __forceinline__ double i128_to_double_scaled(__int128 v, int k) {
-  if (v == 0) return 0.0;
-  const bool neg = v < 0;
-  const unsigned __int128 mag = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-  const int L = bitlen_u128(mag);
-  uint64_t m;
-  int e2 = L - 1 + k;                            // value in [2^e2, 2^(e2+1))
-  if (L <= 53) {
-    m = (uint64_t)mag << (53 - L);
-  } else {
-    const int s = L - 53;
-    m = (uint64_t)(mag >> s);
-    const unsigned __int128 rem = mag & ((((unsigned __int128)1) << s) - 1);
-    const unsigned __int128 half = ((unsigned __int128)1) << (s - 1);
-    if (rem > half || (rem == half && (m & 1))) {
-      m += 1;
-      if (m == (1ull << 53)) { m >>= 1; e2 += 1; }
-    }
-  }
-  const int be = e2 + 1023;
-  if (be >= 1 && be <= 2046)
-    return __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
-  const double d = ldexp((double)m, e2 - 52);   // m is exact in FP64
-  return neg ? -d : d;
+__device__ __forceinline__ int64_t fx_round_norm(uint64_t Nh, bool Ns, int w) {
+  if (w < 0) return 0;                           // below 1/2
+  if (w == 0) return (Nh == (1ull << 63) && !Ns) ? 0 : 1;   // in [1/2, 1): a tie only at 1/2
+  const int sh = 64 - w;
+  const uint64_t q = Nh >> sh;
+  const uint64_t rem = Nh & ((1ull << sh) - 1);
+  const uint64_t half = 1ull << (sh - 1);
+  return (int64_t)(q + ((rem > half) || (rem == half && (Ns || (q & 1ull)))));
 }
 
 __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
@@ -515,12 +500,15 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
       }
       // r_j = b_j - S_j 2^sc is formed exactly in 128 bits (b_j put at the
       // dot's scale; bits of b_j below 2^sc are rounded) and rounded once;
-      // rho_j's fixed point is then taken from the exact R_j.  A b_j too
+      // rho_j's fixed point is then taken from the exact R_j.  |R_j| is
+      // normalised once (Nh: its top 64 bits, Ns: whether any bit below them
+      // is set), and both roundings -- to 53 bits for r_j, to the CTA's fixed
+      // point for P_j -- are taken from (Nh, Ns), ties to even.  A b_j too
       // large for that scale (or non-finite) takes the FP64 route.
-      uint64_t rbits = 0;
-      int qj = kNoExp;
-      bool exact = false;
-      __int128 Rx = 0;
+      uint64_t rbits = 0, Nh = 0;
+      int qj = kNoExp, Lx = 0;
+      bool exact = false, Ns = false, neg = false;
+      double rj = 0.0;
       const int sc = ej + xtop - 2154;
       if (lane < rows) {
         __int128 Sj = 0;
@@ -531,33 +519,37 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
         int beb;
         fx_decode(bb, Mb, beb);
         const int shb = beb - 1075 - sc;
-        double rj;
         if (((bb >> 52) & 0x7FF) != 0x7FF && shb <= 72) {
           __int128 Bj = (shb >= 0) ? ((__int128)Mb << shb) : (__int128)fx_round_shift(Mb, shb);
           if (bb >> 63) Bj = -Bj;
-          Rx = Bj - Sj;
+          const __int128 Rx = Bj - Sj;
           exact = true;
-          rj = i128_to_double_scaled(Rx, sc);
+          neg = Rx < 0;
+          const unsigned __int128 mag = neg ? (unsigned __int128)(-Rx) : (unsigned __int128)Rx;
+          if (mag != 0) {
+            Lx = bitlen_u128(mag);
+            const unsigned __int128 N = mag << (128 - Lx);
+            Nh = (uint64_t)(N >> 64);
+            Ns = (uint64_t)N != 0;
+            rj = fx_round53(Nh, Ns, neg, Lx - 1 + sc);
+          }
         } else {
           rj = bj - scale2(i128_to_double(Sj), sc);
         }
-        rn2 += rj * rj;
-        if (a.r_prev) { const double dl = rj - rpj; dn2 += dl * dl; }
-        if (a.r_out) a.r_out[row0 + lane] = rj;
         rbits = (uint64_t)__double_as_longlong(rj);
         const int ex = (int)((rbits >> 52) & 0x7FF);
         if (ex == 0x7FF) {
           bad = 1;
           exact = false;
         } else if (exact) {
-          if (Rx != 0) qj = bitlen_u128(Rx < 0 ? (unsigned __int128)(-Rx) : (unsigned __int128)Rx) + sc + 1022 + ej;
+          if (Lx) qj = Lx + sc + 1022 + ej;
         } else if (rj != 0.0) {
           qj = (ex ? ex : 1) + ej;
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&pfree[slot]);
-      const int qmax = warp_max_int(qj);
+      const int qmax = __reduce_max_sync(0xffffffffu, qj);
       // the running exponent after tile k - 1 (the other warp's)
       int Eprev = kNoExp;
       if (k >= 1) {
@@ -580,7 +572,8 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
       if (lane < tr) {
         int64_t P = 0;
         if (qj != kNoExp && exact) {
-          P = round_shift_i128(Rx, sc + ej + 1077 - Ecta);      // |P| < 2^55 since qj <= Ecta
+          P = fx_round_norm(Nh, Ns, Lx + sc + ej + 1077 - Ecta);   // |P| <= 2^55 since qj <= Ecta
+          if (neg) P = -P;
         } else if (qj != kNoExp) {
           uint64_t M;
           int be;
@@ -593,6 +586,12 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
       if (lane == 0) rshift[s] = shift;
       __syncwarp();
       if (lane == 0) mbar_arrive(&rready[s]);
+      // off the hand-off path: r_out and the squared norms
+      if (lane < rows) {
+        rn2 += rj * rj;
+        if (a.r_prev) { const double dl = rj - rpj; dn2 += dl * dl; }
+        if (a.r_out) a.r_out[row0 + lane] = rj;
+      }
     }
     rn2 = warp_sum(rn2);
     dn2 = warp_sum(dn2);
