@@ -55,7 +55,9 @@
 // barrier is left waiting).  Measured at m = 2e6, n = 1000 on the way:
 // eight row and eight column warps, 4.47 ms against 4.24 with four each;
 // one barrier per 256-column box instead of per tile (the row warps start on
-// a tile's first box), 3.69 against 3.22 ms.
+// a tile's first box), 3.69 against 3.22 ms; tiles of 4 rows with 6 stages
+// and three epilogue warps, 4.52 against 3.22 ms (the per-tile hand-offs
+// cost more than the deeper ring won); eight row warps, 3.31 against 3.04 ms.
 #include "ls_internal.cuh"
 
 namespace lsk {
@@ -192,8 +194,19 @@ __device__ __forceinline__ bool fx_try(uint64_t* bar, uint32_t parity, uint32_t 
   return ok != 0;
 }
 
+// Non-blocking probe of a phase (cheaper than try_wait when it has completed).
+__device__ __forceinline__ bool fx_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 __device__ __forceinline__ bool fx_wait(uint64_t* bar, uint32_t parity, unsigned long long ns) {
-  if (fx_try(bar, parity, 20000u)) return true;   // the clock is read only when the phase is not complete yet
+  if (fx_test(bar, parity)) return true;   // the clock is read only when the phase is not complete yet
   const uint64_t deadline = gtimer() + ns;
   for (;;) {
     if (fx_try(bar, parity, 20000u)) return true;
@@ -378,6 +391,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
         // the TMA's zero fill and x is zero-padded there, so all lanes run
         // the same compile-time loop (NB blocks of eight columns per box)
         constexpr int NB = 256 / (8 * CS);
+        static_assert(NB >= 1 && NB * 8 * CS == 256, "the row lanes must cover a box");
         for (int qb = 0; qb < nbox; ++qb) {
           const int2* bp = tl + (size_t)qb * tr * 256 + rl * 256 + rho;
           const int4* xp = xs + qb * 256 + rho;
@@ -658,15 +672,24 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
 #pragma unroll
       for (int u = 0; u < NPT2; ++u) W[u] = (sh >= 120) ? (__int128)0 : (W[u] >> sh);
     }
-    // column tc + 128 u of a boxed row sits in box u / 2 at tc + 128 (u % 2)
-    const int2* cb = tl + (kBoxed ? tc : 0);
+    // boxed rows: lane tc holds the column pairs 2 tc + 256 v (box v), so
+    // one 16-byte load brings columns u = 2 v and 2 v + 1
+    const int2* cb = tl + (kBoxed ? 2 * tc : 0);
     auto col_row = [&](int r) {
       const int2 pv = rs[r];
       const int ps = pv.x + pv.y;
       int2 av[NPT2];
+      if (kBoxed) {
 #pragma unroll
-      for (int u = 0; u < NPT2; ++u)                  // all loads first
-        av[u] = kBoxed ? cb[r * 256 + (u >> 1) * (tr * 256) + 128 * (u & 1)] : tl[r * pitch + off[u]];
+        for (int v = 0; v < NPT2 / 2; ++v) {
+          const int4 pr = *reinterpret_cast<const int4*>(cb + r * 256 + v * (tr * 256));
+          av[2 * v] = make_int2(pr.x, pr.y);
+          av[2 * v + 1] = make_int2(pr.z, pr.w);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < NPT2; ++u) av[u] = tl[r * pitch + off[u]];
+      }
 #pragma unroll
       for (int u = 0; u < NPT2; ++u) {
         T2[u] = mad_wide(av[u].y, pv.y, T2[u]);
@@ -691,7 +714,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
   fold();
 #pragma unroll
   for (int u = 0; u < NPT2; ++u) {
-    const int c = tc + kCT * u;
+    const int c = kBoxed ? 2 * tc + 256 * (u >> 1) + (u & 1) : tc + kCT * u;
     if (c < n) {
       out[2 * c] = (long long)(unsigned long long)W[u];
       out[2 * c + 1] = (long long)(W[u] >> 64);
