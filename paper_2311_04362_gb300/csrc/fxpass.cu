@@ -42,7 +42,10 @@
 // bit-identical run to run.
 //
 // k_fx_pass is warp-specialized (11 warps, one CTA per SM): a TMA producer
-// warp streams row tiles of the fixed-point A into a ring of shared stages;
+// warp streams row tiles of the fixed-point A into a ring of shared stages,
+// and asks L2 for the CTA's next tile as it loads one (cp.async.bulk
+// .prefetch: with three 64 KB stages held by the pipeline, the load that
+// refills a stage then comes from L2 instead of waiting on DRAM);
 // warps 0-3 form the exact partial row dots of tile k (each lane two rows of
 // the tile, in four independent accumulator sets per row, so that the
 // integer multiply-add chains overlap) and hand them over through a two-slot
@@ -349,6 +352,14 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
         mbar_arrive_expect_tx(&full[s], tile_bytes);
         int2* dst = tiles + (size_t)s * stage_elems;
         for (int q = 0; q < nbox; ++q) tma_load_2d(dst + (size_t)q * tr * boxw, &map, q * boxw, t * tr, &full[s]);
+        // pull the CTA's next tile into L2 now, so that its load (once a
+        // stage frees) comes from L2; DRAM is read once either way
+        const int tp = t + (1) * gridDim.x;
+        if (tp < a.ntiles)
+          for (int q = 0; q < nbox; ++q)
+            asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)&map),
+                         "r"(q * boxw), "r"(tp * tr)
+                         : "memory");
       }
       // drain: every issued copy lands before the CTA can exit
       const int issued = k;
