@@ -735,27 +735,34 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
 
 // Sum the per-CTA fixed-point partials exactly (aligned to the largest CTA
 // exponent) and round once: c[k] = 2^(E - 2126) sum_p W_kp; the squared norms
-// are FP64 sums in CTA order.  Writes c (n) and norms (2); a non-finite x or
-// r in any CTA makes c and norms NaN.
+// are FP64 sums over the CTAs in a fixed tree order.  One warp per output
+// (k < n: c[k]; k = n, n + 1: the norms); the lanes take the CTAs p = lane,
+// lane + 32, ...  The integer sums are exact, so their order does not matter.
+// Writes c (n) and norms (2); a non-finite x or r in any CTA makes c and
+// norms NaN.
 __global__ void k_fx_reduce(const long long* __restrict__ part, int nparts, int n, double* __restrict__ c,
                             double* __restrict__ norms, const IterState* st) {
   if (st && st->done) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n + 2) return;
+  const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (k >= n + 2) return;                             // whole warps leave together
   const size_t stride = 2 * (size_t)n + 4;
   int flags = 0;
-  for (int p = 0; p < nparts; ++p) flags |= (int)part[p * stride + 2 * n + 3];
+  for (int p = lane; p < nparts; p += 32) flags |= (int)part[p * stride + 2 * n + 3];
+  flags = (int)__reduce_or_sync(0xffffffffu, (unsigned)flags);
   if (k >= n) {
     double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += __longlong_as_double(part[p * stride + 2 * n + 1 + (k - n)]);
-    norms[k - n] = flags ? __longlong_as_double(0x7FF8000000000000ll) : s;
+    for (int p = lane; p < nparts; p += 32) s += __longlong_as_double(part[p * stride + 2 * n + 1 + (k - n)]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) norms[k - n] = flags ? __longlong_as_double(0x7FF8000000000000ll) : s;
     return;
   }
   int E = kNoExp;
-  for (int p = 0; p < nparts; ++p) E = max(E, (int)part[p * stride + 2 * n]);
+  for (int p = lane; p < nparts; p += 32) E = max(E, (int)part[p * stride + 2 * n]);
+  E = __reduce_max_sync(0xffffffffu, E);
   __int128 sum = 0;
   if (E != kNoExp) {
-    for (int p = 0; p < nparts; ++p) {
+    for (int p = lane; p < nparts; p += 32) {
       const int Ep = (int)part[p * stride + 2 * n];
       if (Ep == kNoExp) continue;
       const int sh = E - Ep;
@@ -764,10 +771,14 @@ __global__ void k_fx_reduce(const long long* __restrict__ part, int nparts, int 
                          (__int128)(unsigned long long)part[p * stride + 2 * k];
       sum += w >> sh;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += shfl_xor_i128(sum, o);
   }
-  double v = (E == kNoExp) ? 0.0 : scale2(i128_to_double(sum), E - 2126);
-  if (flags) v = __longlong_as_double(0x7FF8000000000000ll);
-  c[k] = v;
+  if (lane == 0) {
+    double v = (E == kNoExp) ? 0.0 : scale2(i128_to_double(sum), E - 2126);
+    if (flags) v = __longlong_as_double(0x7FF8000000000000ll);
+    c[k] = v;
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -860,8 +871,8 @@ cudaError_t launch_fx_pass(ls_ctx* ctx, const CUtensorMap& map, const FxGeom& g,
 
 cudaError_t launch_fx_reduce(ls_ctx* ctx, const long long* part, int nparts, int64_t n, double* c, double* norms,
                              const IterState* st) {
-  const int threads = 128;
-  const int grid = (int)((n + 2 + threads - 1) / threads);
+  const int threads = 256;                          // eight outputs per block, a warp each
+  const int grid = (int)((n + 2 + 7) / 8);
   k_fx_reduce<<<grid, threads, 0, ctx->stream>>>(part, nparts, (int)n, c, norms, st);
   ++ctx->launches;
   return cudaGetLastError();
