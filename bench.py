@@ -550,11 +550,31 @@ def small_case(ctx, stream, args):
     t0 = time.perf_counter()
     xo, io = oracle.solve(P["A"], P["b"], d, c["zeta"], c["q"], c["seed"], extra=EXTRA_ITERS)
     t_or = time.perf_counter() - t0
+    # throughput: the same problem as `copies` members of one ls_solve_batched
+    # call (embedding seed = member index; A and b shared, x per member)
+    copies = 2048
+    xs_b = torch.empty((copies, n), dtype=torch.float64, device="cuda")
+    members = [dict(A=A, b=b, x=xs_b[i], m=m, n=n, lda=n, d=d, seed=i) for i in range(copies)]
+    ctx.ls_solve_batched(members, c["zeta"], c["q"])
+    bsteps = max(2, args.steps // 2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(bsteps):
+        binf = ctx.ls_solve_batched(members, c["zeta"], c["q"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1) / bsteps
+    fe_b = [oracle.forward_error(xs_b[i].cpu().numpy(), P["x"]) for i in range(0, copies, copies // 16)]
+    batched = {"copies": copies, "value": copies * 1e3 / bms, "unit": UNIT, "ms_per_call": bms,
+               "iters_mean": float(np.mean([binf[i].iters for i in range(copies)])),
+               "fe_over_qr_max_of_16": max(fe_b) / fe_qr,
+               "kind": "one ls_solve_batched call of the problem repeated, embedding seeds 0..copies-1"}
     cores = len(os.sched_getaffinity(0))
     with mp.get_context("spawn").Pool(cores, initializer=_one_thread) as pool:
         ts = pool.map(_oracle_small_solve_worker, range(cores))
     return {"workload": "small single FP64 problem: m=4000, n=50, kappa=1e10, ||r||=1e-6, d=20n=1000, zeta=8, "
                         "seed 0, q<=100",
+            "batched": batched,
             "value": 1e3 / ms, "unit": UNIT, "ms_per_solve": ms, "iters": info.iters, "fe": fe, "fe_qr": fe_qr,
             "phase_ms": {"sketch": info.ms_sketch, "factor": info.ms_factor, "iterate": info.ms_iterate},
             "launches": info.launches,

@@ -705,7 +705,12 @@ int ts_cluster_size() {
 }
 
 static cudaError_t launch_ts(ls_ctx* ctx, const void* f1, const void* f2, const StepArgs& a) {
-  const int P = ts_cluster_size();
+  // the smallest power-of-two cluster, up to the largest that fits, that
+  // still gives every CTA at most one block of 32 rows: small n then meets
+  // fewer CTAs at every cluster barrier and pushes to fewer
+  int P = ts_cluster_size();
+  const int nb = (a.n + 31) / 32;
+  while (P > 1 && P / 2 >= nb) P /= 2;
   const int pp = ts_slots(a.n, P);
   if (pp == 0 || a.n > kTsMaxN) return cudaErrorInvalidValue;
   StepArgs aa = a;
