@@ -58,9 +58,9 @@ def _code_only(text: str) -> str:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the fixed-point pass kernel's code (its device helpers and the
-    k_fx_pass body in fxpass.cu plus the shared device helpers it uses),
-    comments excluded."""
+    """Hash of the fixed-point pass kernel's code (the k_fx_pass part of
+    fxpass.cu, the integer arithmetic of fxarith.cuh and the shared device
+    helpers of ls_internal.cuh), comments excluded."""
     csrc = os.path.join(ROOT, "paper_2311_04362_gb300", "csrc")
     with open(os.path.join(csrc, "fxpass.cu")) as fh:
         text = fh.read()
@@ -68,6 +68,8 @@ def kernel_source_hash() -> str:
     with open(os.path.join(csrc, "ls_internal.cuh")) as fh:
         helpers = fh.read()
     h.update(_code_only(helpers[:helpers.index("// -------------------------------------------------------------------- context")]).encode())
+    with open(os.path.join(csrc, "fxarith.cuh")) as fh:
+        h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
