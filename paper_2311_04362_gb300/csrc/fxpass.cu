@@ -692,7 +692,15 @@ FxGeom fx_geometry(const ls_ctx* ctx, int64_t n, int64_t m) {
     g.tr = (g.nbox <= 2) ? 16 : 8;
   }
   const size_t stage = (size_t)g.tr * g.nbox * g.boxw * sizeof(int2);
-  g.stages = (int)std::max<size_t>(2, std::min<size_t>(4, (192 * 1024) / stage));
+  {
+    // as many stages as fit beside the fixed parts (p1, xs, per-stage slots
+    // and barriers; at most 8), within the 227 KB a CTA may use
+    const size_t xl = (g.nbox > 1) ? (size_t)g.nbox * 256 : (size_t)n;
+    const size_t fixed = (size_t)2 * kFxRW * g.tr * 16 + xl * 16 + 4 * 8 + 128 + 1024;
+    const size_t per_stage = stage + (size_t)g.tr * 8 + 4 + 4 * 8;
+    const size_t room = (227 * 1024 > fixed) ? (227 * 1024 - fixed) : 0;
+    g.stages = (int)std::max<size_t>(2, std::min<size_t>(8, room / per_stage));
+  }
   const int64_t ntiles = (m + g.tr - 1) / g.tr;
   g.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ntiles));
   const size_t xlen = (g.nbox > 1) ? (size_t)g.nbox * 256 : (size_t)n;
