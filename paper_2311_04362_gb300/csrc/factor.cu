@@ -425,9 +425,15 @@ __global__ void __launch_bounds__(256, 1) k_householder_blocked(HhArgs a) {
 // trailing columns, taking (32-column group, row chunk) tasks from a shared
 // counter.  w is 2 or 4 while the update is long; once it is short the
 // panel is factored by all 8 warps after the update.
-// The panel is latency-bound (two grid barriers per column) and the update
-// is FP64-bound, so the two fill each other's idle time.  Panel 0 is factored
-// by all warps.  Row dots of a panel column are summed per warp slice of the
+// The panel is latency-bound and the update FP64-bound, so the two fill each
+// other's idle time.  A panel column takes one grid barrier: every CTA
+// publishes, for the column x below its diagonal row, the partial sum of
+// squares and the partial dots x^T a_jj with the later panel columns (and
+// the owner of the diagonal row publishes that row), so that after the
+// barrier every CTA has the reflector and v^T a_jj = a_jj,k + scal x^T a_jj
+// at once (two barriers per column before: 46.0 -> 43.4 ms at d = 20,000,
+// n = 1000, with the lookahead thresholds retuned).  Panel 0 is factored by
+// all warps.  Row dots of a panel column are summed per warp slice of the
 // rows, then over warps in warp order; CTA partials in CTA-range order.
 static constexpr int kLaTasksPerGroup = 8;
 
@@ -446,11 +452,13 @@ __global__ void __launch_bounds__(256, 1) k_householder_la(HhArgs a) {
   double* pbuf0 = sm;                                 // two panel buffers, kNB columns x ldp
   double* pbuf1 = sm + (size_t)kNB * ldp;
   double* Gs = sm + (size_t)2 * kNB * ldp;            // W' multipliers, kNB x kNB
-  double* pnorm = a.part;                    // [P]
-  double* alpha_slot = a.part + P;           // [1]
   double* pdot = a.part + P + 8;             // [P][kNB]
   double* pW = pdot + (size_t)P * kNB;       // [P][kNB][ncols]
   double* pG = pW + (size_t)P * kNB * ncols; // [P][kNB*kNB]
+  // column kk of a panel uses buffer kk & 1 of the dot partials and of row k
+  // (a CTA writes column kk + 2's only after every CTA has read column kk's)
+  double* rowk0 = pG + (size_t)P * kNB * kNB;     // [2][kNB]: row k of the panel
+  double* pdot1 = rowk0 + 2 * kNB;                  // second buffer of pdot, [P][kNB]
   double* Gred = a.Wp + (size_t)kNB * ncols + 8;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* B = a.B;
@@ -488,31 +496,34 @@ __global__ void __launch_bounds__(256, 1) k_householder_la(HhArgs a) {
     gsync(nw);
     return s_gok != 0;
   };
-  // sum over the threads of warps 0..nw-1, in warp order
-  auto gsum = [&](double v, int nw) -> double {
-    v = warp_sum(v);
-    if (lane == 0) s_red[warp][0] = v;
+  // Partials of panel column kk (global k) over own rows > k: lane 0 the sum
+  // of squares, lane l its dot with panel column kk + l; the owner of row k
+  // publishes row k of the panel (alpha and the a_jj,k).  One grid barrier
+  // then gives every CTA the reflector and all its dots at once:
+  // v^T a_jj = a_jj,k + scal (x^T a_jj) with x the column below row k.
+  auto col_partials = [&](const double* Pn, int kk, int k, int nbp, int nw) {
+    double* pd = (kk & 1) ? pdot1 : pdot;
+    double* rowk = rowk0 + (kk & 1) * kNB;
+    const int i0 = (int)max((int64_t)0, (int64_t)k + 1 - r0);
+    const int len = max(0, nrow - i0);
+    const int ia = i0 + (len * warp) / nw, ib = i0 + (len * (warp + 1)) / nw;
+    const int jj = kk + lane;
+    double s = 0.0;
+    if (jj < nbp)
+      for (int i = ia; i < ib; ++i) s += Pn[kk * ldp + i] * Pn[jj * ldp + i];
+    s_red[warp][lane] = s;
     gsync(nw);
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += s_red[w][0];
-    gsync(nw);
-    return t;
-  };
-  // norm partial of column kk (global k) over own rows > k; the owner publishes alpha
-  auto norm_partial = [&](const double* Pn, int kk, int k, int nw) {
-    double ss = 0.0;
-    for (int i = threadIdx.x; i < nrow; i += 32 * nw)
-      if (r0 + i > k) { const double v = Pn[kk * ldp + i]; ss += v * v; }
-    ss = gsum(ss, nw);
-    if (threadIdx.x == 0) {
-      __stcg(pnorm + p, ss);
-      if (k >= r0 && k < r1) __stcg(alpha_slot, Pn[kk * ldp + (k - r0)]);
+    if (warp == 0 && jj < nbp) {
+      double d = 0.0;
+      for (int w = 0; w < nw; ++w) d += s_red[w][lane];
+      __stcg(pd + (size_t)p * kNB + jj, d);
+      if (k >= r0 && k < r1) __stcg(rowk + jj, Pn[jj * ldp + (k - r0)]);
     }
   };
 
   // Factor the panel of columns k0 .. k0+nbp-1 (own rows) into Pn with warps
-  // 0..nw-1; the CTA's other warps do not take part.  False: rank
-  // deficiency or a timed-out barrier (status set).
+  // 0..nw-1; the CTA's other warps do not take part.  One grid barrier per
+  // column.  False: rank deficiency or a timed-out barrier (status set).
   auto factor_panel = [&](double* Pn, int k0, int nbp, int nw) -> bool {
     const int nthr = 32 * nw;
     for (int e = threadIdx.x; e < kNB * nrow; e += nthr) {
@@ -520,29 +531,41 @@ __global__ void __launch_bounds__(256, 1) k_householder_la(HhArgs a) {
       Pn[c * ldp + i] = (c < nbp) ? B[(r0 + i) + (int64_t)(k0 + c) * ldb] : 0.0;
     }
     gsync(nw);
-    norm_partial(Pn, 0, k0, nw);
+    col_partials(Pn, 0, k0, nbp, nw);
     g_arrive(nw);
     for (int kk = 0; kk < nbp; ++kk) {
       const int k = k0 + kk;
       if (!g_wait(nw)) return false;
+      // sums over CTAs: warp w takes a contiguous range of CTAs, lane l the
+      // entry kk + l; then the reflector and the multipliers w_jj = tau v^T a_jj
+      const int jj = kk + lane;
+      const double* pd = (kk & 1) ? pdot1 : pdot;
+      const double* rowk = rowk0 + (kk & 1) * kNB;
+      double s = 0.0;
+      if (jj < nbp)
+        for (int q = (P * warp) / nw; q < (P * (warp + 1)) / nw; ++q) s += __ldcg(pd + (size_t)q * kNB + jj);
+      s_red[warp][lane] = s;
+      gsync(nw);
       if (warp == 0) {
-        double t = 0.0;
-        for (int q = lane; q < P; q += 32) t += __ldcg(pnorm + q);
-        t = warp_sum(t);
+        double d = 0.0;
+        for (int w = 0; w < nw; ++w) d += s_red[w][lane];
+        const double t = __shfl_sync(0xffffffffu, d, 0);
+        const double alpha = __ldcg(rowk + kk);
+        double beta, tau, scal;
+        if (t == 0.0) {
+          beta = alpha; tau = 0.0; scal = 1.0;
+        } else {
+          const double h = sqrt(alpha * alpha + t);
+          beta = (alpha >= 0.0) ? -h : h;
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
         if (lane == 0) {
-          const double alpha = __ldcg(alpha_slot);
-          double beta, tau, scal;
-          if (t == 0.0) {
-            beta = alpha; tau = 0.0; scal = 1.0;
-          } else {
-            const double h = sqrt(alpha * alpha + t);
-            beta = (alpha >= 0.0) ? -h : h;
-            tau = (beta - alpha) / beta;
-            scal = 1.0 / (alpha - beta);
-          }
           s_par[1] = tau; s_par[2] = scal;
           s_tau[kk] = tau; s_beta[kk] = beta;
           s_bad = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+        } else if (jj < nbp) {
+          s_w[jj] = (tau != 0.0) ? tau * (__ldcg(rowk + jj) + scal * d) : 0.0;
         }
       }
       gsync(nw);
@@ -551,54 +574,20 @@ __global__ void __launch_bounds__(256, 1) k_householder_la(HhArgs a) {
         return false;
       }
       const double tau = s_par[1], scal = s_par[2];
+      // v = [1; x scal] on own rows >= k; a_jj -= w_jj v for the later columns
       for (int i = threadIdx.x; i < nrow; i += nthr) {
         const int64_t g = r0 + i;
-        if (g == k) Pn[kk * ldp + i] = 1.0;
-        else if (g > k && tau != 0.0) Pn[kk * ldp + i] *= scal;
+        if (g < k) continue;
+        const double x = Pn[kk * ldp + i];
+        const double v = (g == k) ? 1.0 : ((tau != 0.0) ? x * scal : x);
+        if (tau != 0.0)
+          for (int c = kk + 1; c < nbp; ++c) Pn[c * ldp + i] -= s_w[c] * v;
+        Pn[kk * ldp + i] = v;
       }
       gsync(nw);
       if (kk + 1 < nbp) {
-        // dots v^T a_jj: lane = column jj, warp = slice of the rows >= k
-        const int i0 = (int)max((int64_t)0, (int64_t)k - r0);
-        const int len = max(0, nrow - i0);
-        const int ia = i0 + (len * warp) / nw, ib = i0 + (len * (warp + 1)) / nw;
-        const int jj = kk + 1 + lane;
-        double s = 0.0;
-        if (jj < nbp && tau != 0.0)
-          for (int i = ia; i < ib; ++i) s += Pn[kk * ldp + i] * Pn[jj * ldp + i];
-        s_red[warp][lane] = s;
-        gsync(nw);
-        if (warp == 0 && jj < nbp) {
-          double d = 0.0;
-          for (int w = 0; w < nw; ++w) d += s_red[w][lane];
-          __stcg(pdot + (size_t)p * kNB + jj, d);
-        }
+        col_partials(Pn, kk + 1, k + 1, nbp, nw);
         g_arrive(nw);
-        if (!g_wait(nw)) return false;
-        // tau (v^T a_jj) summed over CTAs: warp w takes a contiguous range of CTAs
-        s = 0.0;
-        if (jj < nbp)
-          for (int q = (P * warp) / nw; q < (P * (warp + 1)) / nw; ++q) s += __ldcg(pdot + (size_t)q * kNB + jj);
-        s_red[warp][lane] = s;
-        gsync(nw);
-        if (warp == 0 && jj < nbp) {
-          double d = 0.0;
-          for (int w = 0; w < nw; ++w) d += s_red[w][lane];
-          s_w[jj] = tau * d;
-        }
-        gsync(nw);
-        if (tau != 0.0)
-          for (int i = threadIdx.x; i < nrow; i += nthr)
-            if (r0 + i >= k) Pn[(kk + 1) * ldp + i] -= s_w[kk + 1] * Pn[kk * ldp + i];
-        gsync(nw);
-        norm_partial(Pn, kk + 1, k + 1, nw);
-        g_arrive(nw);
-        if (tau != 0.0) {
-          for (int e = threadIdx.x; e < (nbp - kk - 2) * nrow; e += nthr) {
-            const int jc = kk + 2 + e / nrow, i = e % nrow;
-            if (r0 + i >= k) Pn[jc * ldp + i] -= s_w[jc] * Pn[kk * ldp + i];
-          }
-        }
       }
     }
     gsync(nw);
@@ -718,11 +707,10 @@ __global__ void __launch_bounds__(256, 1) k_householder_la(HhArgs a) {
     const int k1 = k0 + kNB;
     const int nbp1 = (k1 < n) ? min(kNB, n - k1) : 0;
     // warps on the next panel: few while the update is long, all of them
-    // (no overlap) once it is short (measured at d = 20,000, n = 1000: a
-    // 2-warp panel takes ~0.75 ms, an 8-warp one ~0.36 ms, the update of
-    // 31 groups ~1 ms)
+    // (no overlap) once it is short (thresholds measured at d = 20,000,
+    // n = 1000 with one grid barrier per panel column)
     const int grest = ngroups - 1;
-    const int nw1 = (grest >= 20) ? 2 : (grest >= 10) ? 4 : 8;
+    const int nw1 = (grest >= 12) ? 2 : (grest >= 5) ? 4 : 8;
     if (nbp1 > 0 && nw1 < 8 && warp < nw1) {
       if (!factor_panel(cur ? pbuf0 : pbuf1, k1, nbp1, nw1) && threadIdx.x == 0) s_abort = 1;
     }
@@ -739,7 +727,7 @@ __global__ void __launch_bounds__(256, 1) k_householder_la(HhArgs a) {
     __syncthreads();
     if (s_abort) return;
     if (nbp1 > 0 && nw1 == 8 && !factor_panel(cur ? pbuf0 : pbuf1, k1, nbp1, 8)) return;
-    if (nbp1 > 0 && nw1 < 8 && warp >= nw1) mb.epoch += 2u * (unsigned int)nbp1 - 1u;   // the panel's grid barriers
+    if (nbp1 > 0 && nw1 < 8 && warp >= nw1) mb.epoch += (unsigned int)nbp1;   // the panel's grid barriers
     cur ^= 1;
   }
 }
@@ -967,7 +955,7 @@ cudaError_t launch_householder(ls_ctx* ctx, double* B, int64_t d, int64_t n, int
 size_t householder_part_doubles(const ls_ctx* ctx, int64_t d, int64_t n) {
   const size_t P = (size_t)householder_ctas(ctx, d);
   const size_t unblocked = P * (size_t)(n + 2) + 1;
-  const size_t blocked = P + 8 + P * kNB + P * kNB * (size_t)(n + 1) + P * kNB * kNB;
+  const size_t blocked = P + 8 + P * kNB + P * kNB * (size_t)(n + 1) + P * kNB * kNB + 2 * kNB + P * kNB;
   return std::max(unblocked, blocked);
 }
 
