@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_fx_pass(const __grid_constant
         for (int q = 0; q < nbox; ++q) tma_load_2d(dst + (size_t)q * tr * boxw, &map, q * boxw, t * tr, &full[s]);
         // pull the CTA's next tile into L2 now, so that its load (once a
         // stage frees) comes from L2; DRAM is read once either way
-        const int tp = t + (1) * gridDim.x;
+        const int tp = t + gridDim.x;
         if (tp < a.ntiles)
           for (int q = 0; q < nbox; ++q)
             asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)&map),
